@@ -1,0 +1,15 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and by the oracle.
+
+This package holds no arithmetic of the Hermite finite-difference method itself: only
+triangle meshes (jittered, randomly split structured grids standing in for the paper's
+Delaunay meshes, Sec. 3) and the initial/exact states of the paper's test problems
+(isentropic vortex, Sec. 3.1) and of the synthetic workloads (four-quadrant Riemann
+problem, planar Sod, Taylor-Green vortex).
+"""
+from .meshes import jittered_grid, jittered_box_with_ghosts, mesh_summary
+from .states import (GAMMA, isentropic_vortex, four_quadrant, planar_sod, taylor_green,
+                     uniform_state, prim_to_cons)
+
+__all__ = ["jittered_grid", "jittered_box_with_ghosts", "mesh_summary", "GAMMA",
+           "isentropic_vortex", "four_quadrant", "planar_sod", "taylor_green",
+           "uniform_state", "prim_to_cons"]

@@ -1,0 +1,97 @@
+"""Seeded jittered, randomly split structured triangle meshes.
+
+The paper's tests run on Delaunay meshes of a square (Sec. 3.1: 3957-36408 nodes; Sec. 3.3:
+3970-35458 nodes) that are not distributed with it.  These generators stand in for them: a
+structured vertex grid whose vertices are jittered by U(-j*h, j*h) per axis and whose quads are
+split along a Bernoulli(0.5) random diagonal.  Triangles are counter-clockwise.
+
+Two kinds of axis are supported:
+  * periodic: n vertices at a + i*L/n, i = 0..n-1, quads wrap around;
+  * bounded:  n physical vertices at a + i*(b-a)/(n-1) (the boundary lines are not jittered),
+              plus `ghost` layers of unjittered ghost vertices outside [a, b].  Each ghost vertex
+              names a donor (the nearest physical vertex, by clamping the grid index) and flags
+              which derivative components are zeroed when it is refreshed (bit 0: the x
+              derivatives, bit 1: the y derivatives, i.e. the derivative normal to the boundary
+              the ghost lies beyond).
+
+Vertex ids are row-major over the (possibly ghost-extended) grid.  Random draws, in order from
+numpy's PCG64(seed): x jitter for all vertices, y jitter for all vertices, one diagonal bit
+per quad.
+"""
+import numpy as np
+
+
+def _axis(n, lo, hi, periodic, ghost):
+    """Grid coordinates, physical mask and clamp index along one axis."""
+    if periodic:
+        h = (hi - lo) / n
+        idx = np.arange(n)
+        return lo + idx * h, np.ones(n, bool), idx, h, np.zeros(n, bool)
+    h = (hi - lo) / (n - 1)
+    idx = np.arange(-ghost, n + ghost)
+    coord = lo + idx * h
+    physical = (idx >= 0) & (idx <= n - 1)
+    boundary = (idx == 0) | (idx == n - 1)
+    return coord, physical, np.clip(idx, 0, n - 1) + ghost, h, boundary
+
+
+def _grid(nx, ny, xr, yr, periodic_x, periodic_y, ghost, jitter, seed):
+    cx, px, clx, hx, bx = _axis(nx, xr[0], xr[1], periodic_x, ghost)
+    cy, py, cly, hy, by = _axis(ny, yr[0], yr[1], periodic_y, ghost)
+    NX, NY = len(cx), len(cy)
+    V = NX * NY
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jx = rng.uniform(-1.0, 1.0, V) * (jitter * hx)
+    jy = rng.uniform(-1.0, 1.0, V) * (jitter * hy)
+    QX = NX if periodic_x else NX - 1
+    QY = NY if periodic_y else NY - 1
+    diag = rng.integers(0, 2, QX * QY)
+
+    I, J = np.meshgrid(np.arange(NX), np.arange(NY), indexing="xy")
+    I = I.ravel()
+    J = J.ravel()
+    phys = px[I] & py[J]
+    on_bnd = bx[I] | by[J]
+    jit = phys & ~on_bnd
+    x = cx[I] + np.where(jit, jx, 0.0)
+    y = cy[J] + np.where(jit, jy, 0.0)
+
+    qI, qJ = np.meshgrid(np.arange(QX), np.arange(QY), indexing="xy")
+    qI = qI.ravel()
+    qJ = qJ.ravel()
+    v00 = qJ * NX + qI
+    v10 = qJ * NX + (qI + 1) % NX
+    v01 = ((qJ + 1) % NY) * NX + qI
+    v11 = ((qJ + 1) % NY) * NX + (qI + 1) % NX
+    t0 = np.where(diag[:, None] == 0, np.stack([v00, v10, v11], 1), np.stack([v00, v10, v01], 1))
+    t1 = np.where(diag[:, None] == 0, np.stack([v00, v11, v01], 1), np.stack([v10, v11, v01], 1))
+    tri = np.concatenate([t0, t1]).astype(np.int32)
+
+    ghost_ids = np.nonzero(~phys)[0].astype(np.int32)
+    gI, gJ = I[ghost_ids], J[ghost_ids]
+    donor = (cly[gJ] * NX + clx[gI]).astype(np.int32)
+    flags = ((clx[gI] != gI).astype(np.int32) | ((cly[gJ] != gJ).astype(np.int32) << 1))
+    return {
+        "x": x, "y": y, "tri": tri,
+        "Lx": float(xr[1] - xr[0]), "Ly": float(yr[1] - yr[0]),
+        "periodic_x": bool(periodic_x), "periodic_y": bool(periodic_y),
+        "ghost_ids": ghost_ids, "ghost_donor": donor, "ghost_flags": flags.astype(np.int32),
+        "grid": (NX, NY), "h": (hx, hy), "seed": seed,
+    }
+
+
+def jittered_grid(nx, ny, Lx, Ly, seed, jitter=0.15, x0=0.0, y0=0.0):
+    """Doubly periodic nx-by-ny vertex grid on [x0, x0+Lx) x [y0, y0+Ly), every vertex jittered."""
+    return _grid(nx, ny, (x0, x0 + Lx), (y0, y0 + Ly), True, True, 0, jitter, seed)
+
+
+def jittered_box_with_ghosts(nx, ny, xr, yr, ghost, seed, jitter=0.15, periodic_y=False):
+    """nx-by-ny physical vertices on the closed box xr x yr with `ghost` ghost layers outside
+    each bounded side (y may instead be periodic).  Boundary lines and ghosts are unjittered."""
+    return _grid(nx, ny, xr, yr, False, periodic_y, ghost, jitter, seed)
+
+
+def mesh_summary(mesh):
+    V = len(mesh["x"])
+    return {"vertices": V, "triangles": len(mesh["tri"]), "ghosts": len(mesh["ghost_ids"]),
+            "active": V - len(mesh["ghost_ids"])}

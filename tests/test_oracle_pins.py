@@ -1,0 +1,539 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: closed forms, textbook
+special cases, library routines on reformulated problems, exact rational arithmetic,
+complex-step derivatives, symmetry, or the paper's stated orders of accuracy.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import hfd_oracle as H
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def c1():
+    m = synth.jittered_grid(40, 40, 10.0, 10.0, seed=1)
+    topo = oracle.build_topology(m)
+    return m, topo
+
+
+@pytest.fixture(scope="module")
+def c1_prep(c1):
+    m, topo = c1
+    return oracle.prepare(m, topo=topo)
+
+
+# ------------------------------------------------------------------ basis (Sec. 2.2)
+
+def test_taylor_basis_is_the_printed_p():
+    """Sec. 2.2 prints p(x, y) term by term; its ordering fixes which coefficient is a_2, b_3,
+    a_4, ... in the divergence rows."""
+    x, y = 0.37, -1.21
+    printed = [1, x, y, x * x / 2, x * y, y * y / 2, x ** 3 / 6, x * x * y / 2, x * y * y / 2,
+               y ** 3 / 6, x ** 4 / 24, x ** 3 * y / 6, x * x * y * y / 4, x * y ** 3 / 6,
+               y ** 4 / 24]
+    p, _, _ = oracle.taylor_basis(x, y, 4)
+    np.testing.assert_allclose(p, printed, rtol=1e-15)
+
+
+@pytest.mark.parametrize("deg", [2, 4, 5])
+def test_taylor_basis_derivatives_by_complex_step(deg):
+    x, y, h = 0.73, -0.41, 1e-30
+    _, px, py = oracle.taylor_basis(x, y, deg)
+    cx = oracle.taylor_basis(x + 1j * h, y, deg)[0].imag / h
+    cy = oracle.taylor_basis(x, y + 1j * h, deg)[0].imag / h
+    np.testing.assert_allclose(px, cx, rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(py, cy, rtol=1e-14, atol=1e-15)
+
+
+# ------------------------------------------------------------------ 5-node Hermite LS (Sec. 2.2)
+
+def _quartic(rng):
+    c = rng.standard_normal(15)
+
+    def f(x, y):
+        p, px, py = oracle.taylor_basis(x, y, 4)
+        return c @ p, c @ px, c @ py
+    return f
+
+
+def _squared_conic_taylor(X):
+    """Taylor-basis coefficients (degree 4) of q = c(x, y)^2, c the conic through the 5 points.
+    q and its gradient vanish at every node, so q spans the null space of the 15x15 Hermite
+    matrix of Sec. 2.2 whenever the rank is 14."""
+    from math import factorial
+    M = np.array([[1, x, y, x * x, x * y, y * y] for x, y in X])
+    c = np.linalg.svd(M)[2][-1]
+    mono = {(0, 0): c[0], (1, 0): c[1], (0, 1): c[2], (2, 0): c[3], (1, 1): c[4], (0, 2): c[5]}
+    sq = {}
+    for (a1, b1), v1 in mono.items():
+        for (a2, b2), v2 in mono.items():
+            k = (a1 + a2, b1 + b2)
+            sq[k] = sq.get(k, 0.0) + v1 * v2
+    out = []
+    for d in range(5):
+        for b in range(d + 1):
+            out.append(sq.get((d - b, b), 0.0) * factorial(d - b) * factorial(b))
+    return np.array(out)
+
+
+def test_five_node_min_norm_solution_is_the_projection_off_the_squared_conic():
+    """Sec. 2.2 solves P k = r by SVD.  A degree-4 polynomial that vanishes with its gradient at
+    5 points always exists (the square of the conic through them), so P has rank 14 at most and
+    the SVD solution is the quartic's coefficient vector projected orthogonally to that null
+    vector n: k_1 = k_1(true) - n_1 (n . k)/(n . n).  The null vector is built independently of
+    the oracle (conic through 5 points, squared)."""
+    rng = np.random.default_rng(11)
+    checked = 0
+    for _ in range(60):
+        X = _random_stencil(rng)
+        w, r = oracle.five_node_weights(X, 1.0, near=2, sv_rtol=1e-13)
+        if r < 14:
+            continue
+        k = rng.standard_normal(15)
+        p, px, py = oracle.taylor_basis(X[:, 0], X[:, 1], 4)
+        data = np.stack([k @ p, k @ px, k @ py], 1).ravel()
+        n = _squared_conic_taylor(X)
+        want = k[0] - n[0] * (n @ k) / (n @ n)
+        # undo R4 (which moves the near node's value weight by 1 - sum) to get the SVD row
+        w_svd = w.copy()
+        w_svd[6] -= 1.0 - w[0::3].sum()
+        # a rank-14 SVD solution carries rounding errors of order eps * (sigma_1 / sigma_14)^2
+        Pm = np.zeros((15, 15))
+        Pm[0::3], Pm[1::3], Pm[2::3] = p.T, px.T, py.T
+        S = np.linalg.svd(Pm, compute_uv=False)
+        tol = 1e-12 * (S[0] / S[13]) ** 2
+        assert abs(w_svd @ data - want) < tol * np.abs(data).max()
+        checked += 1
+    assert checked >= 20
+
+
+def test_five_node_straight_uniform_is_1d_hermite_least_squares():
+    """On a straight, uniformly spaced stencil only the x-part of the basis is seen: the value
+    weights are those of the degree-4 least-squares fit to 5 values and 5 slopes (a textbook
+    1D problem, solved here with numpy's lstsq), and the y-derivative weights vanish."""
+    xs = np.array([-2.5, -1.5, -0.5, 0.5, 1.5])
+    rel = np.stack([xs, np.zeros(5)], 1)
+    w, r = oracle.five_node_weights(rel, 1.0, near=2)
+    assert r == 9
+    A = np.zeros((10, 5))
+    for j, x in enumerate(xs):
+        A[2 * j] = [1, x, x * x / 2, x ** 3 / 6, x ** 4 / 24]
+        A[2 * j + 1] = [0, 1, x, x * x / 2, x ** 3 / 6]
+    ref = np.linalg.pinv(A)[0]
+    np.testing.assert_allclose(w[0::3], ref[0::2], atol=1e-13)
+    np.testing.assert_allclose(w[1::3], ref[1::2], atol=1e-13)
+    np.testing.assert_allclose(w[2::3], 0.0, atol=1e-13)
+
+
+def _random_stencil(rng):
+    """Random 5-node stencil of the paper's Monte Carlo test (Sec. 2.2): edge lengths with a
+    15 % standard deviation around the middle edge's length 1, deflection angles N(0, pi/12),
+    random orientation.  Nodes i-2..i+2, the middle edge (i, i+1) centred at the origin."""
+    L = 1.0 + 0.15 * rng.standard_normal(3)
+    th = rng.normal(0.0, np.pi / 12, 3)
+    pts = {2: np.array([-0.5, 0.0]), 3: np.array([0.5, 0.0])}
+    a = 0.0
+    p = pts[2]
+    for k, node in enumerate([1, 0]):
+        a += th[k]
+        p = p + L[k] * np.array([-np.cos(a), -np.sin(a)])
+        pts[node] = p
+    pts[4] = pts[3] + L[2] * np.array([np.cos(th[2]), np.sin(th[2])])
+    X = np.array([pts[k] for k in range(5)])
+    phi = rng.uniform(0, 2 * np.pi)
+    c, s = np.cos(phi), np.sin(phi)
+    return X @ np.array([[c, s], [-s, c]])
+
+
+def test_five_node_monte_carlo_order_is_five():
+    """Sec. 2.2 / Fig. 5: on random stencils the interpolation error shrinks like h^5."""
+    rng = np.random.default_rng(5)
+
+    def f(x, y):
+        v = np.sin(1.3 * x + 0.7) * np.cos(0.9 * y - 0.4) + 0.5 * np.exp(0.3 * x * y)
+        fx = 1.3 * np.cos(1.3 * x + 0.7) * np.cos(0.9 * y - 0.4) + 0.15 * y * np.exp(0.3 * x * y)
+        fy = -0.9 * np.sin(1.3 * x + 0.7) * np.sin(0.9 * y - 0.4) + 0.15 * x * np.exp(0.3 * x * y)
+        return v, fx, fy
+
+    orders = []
+    for _ in range(150):
+        X = _random_stencil(rng)
+        x0 = rng.uniform(-1, 1, 2)
+        errs = []
+        for h in (0.05, 0.025):
+            rel = X * h
+            w, _ = oracle.five_node_weights(rel, h, near=2)
+            P = x0[None] + rel
+            v, fx, fy = f(P[:, 0], P[:, 1])
+            errs.append(abs(w @ np.stack([v, fx, fy], 1).ravel() - f(*x0)[0]))
+        orders.append(np.log2(errs[0] / errs[1]))
+    assert 4.5 <= np.median(orders) <= 5.5
+
+
+def test_five_node_weights_bounded_and_consistent(c1_prep):
+    """R3: every stored scaled weight is below 1 in magnitude; R4: value weights sum to 1."""
+    P = c1_prep
+    assert np.allclose(P.w5[:, :, 0::3].sum(-1), 1.0, atol=1e-13)
+    ell = P.ell_edge[:, None, None]
+    scaled = np.concatenate([P.w5[:, :, 0::3], P.w5[:, :, 1::3] / ell, P.w5[:, :, 2::3] / ell], -1)
+    assert np.abs(scaled).max() < 1.0 + 1e-6
+
+
+# ------------------------------------------------------------------ 3-node candidates (Sec. 2.3)
+
+def _golden_wcns():
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "wcns_e5_candidates.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, *vals = line.split()
+        rows[k] = np.array([float(Fraction(v)) for v in vals])
+    return rows
+
+
+def test_three_node_uniform_straight_is_wcns_e5():
+    """Collinear nodes reduce Eq. (3nodes_intp) to 1D quadratic interpolation; on a uniform
+    grid these are WCNS-E5's candidate interpolations (Deng & Zhang 2000)."""
+    g = _golden_wcns()
+    h = 0.1
+    subs = {"C1": [-2.5, -1.5, -0.5], "C2": [-1.5, -0.5, 0.5], "C3": [-0.5, 0.5, 1.5]}
+    for k, xs in subs.items():
+        rel = np.stack([np.array(xs) * h, np.zeros(3)], 1)
+        near = xs.index(-0.5)
+        np.testing.assert_allclose(oracle.three_node_weights(rel, near), g[k], atol=1e-14)
+
+
+def test_three_node_matches_pinv_and_is_exact_where_it_should_be():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        rel = rng.uniform(-1.5, 1.5, (3, 2))
+        w = oracle.three_node_weights(rel, 1)
+        A = np.array([oracle.taylor_basis(x, y, 2)[0] for x, y in rel])
+        ref = np.linalg.pinv(A)[0]
+        ref[1] += 1.0 - ref.sum()
+        np.testing.assert_allclose(w, ref, atol=1e-12)
+        assert abs(w.sum() - 1.0) < 1e-14                       # constants exact (R4)
+    # collinear nodes through the evaluation point: quadratics along the line exact (Sec. 2.3)
+    d = np.array([np.cos(0.3), np.sin(0.3)])
+    t = np.array([-2.3, -1.1, -0.4]) * 0.2
+    rel = t[:, None] * d[None]
+    w = oracle.three_node_weights(rel, 2)
+    q = 0.7 - 1.3 * t + 2.1 * t * t
+    assert abs(w @ q - 0.7) < 1e-12
+
+
+def test_three_node_order_two_on_bent_stencils():
+    """Sec. 2.3: three non-collinear nodes give a second-order (2D linear) interpolant."""
+    rng = np.random.default_rng(9)
+    orders = []
+    for _ in range(50):
+        X = _random_stencil(rng)[[0, 1, 2]]
+        x0 = rng.uniform(-1, 1, 2)
+        errs = []
+        for h in (0.02, 0.01):
+            P = x0[None] + X * h
+            w = oracle.three_node_weights(X * h, 2)
+            f = np.sin(P[:, 0] + 2 * P[:, 1])
+            errs.append(abs(w @ f - np.sin(x0[0] + 2 * x0[1])))
+        orders.append(np.log2(errs[0] / errs[1]))
+    assert np.median(orders) >= 1.8
+
+
+# ------------------------------------------------------------------ WENO sensor (Sec. 2.3, R2)
+
+def test_weno_weights_linear_weights_on_linear_data_and_limits():
+    g = _golden_wcns()["D"]
+    u = 0.3 + 0.7 * np.arange(5)
+    np.testing.assert_allclose(oracle.weno_weights(*u, 1e-6), g, rtol=1e-14)
+    # a jump inside sub-stencils 2 and 3 only: the first weight takes over
+    o = oracle.weno_weights(0.0, 0.0, 0.0, 1.0, 1.0, 1e-6)
+    assert o[0] > 0.99
+    # a jump inside sub-stencil 1 only: its weight vanishes
+    o = oracle.weno_weights(1.0, 0.0, 0.0, 0.0, 0.0, 1e-6)
+    assert o[0] < 1e-6
+
+
+# ------------------------------------------------------------------ characteristics and flux
+
+def _state(rng):
+    rho = rng.uniform(0.5, 2.0)
+    u, v = rng.uniform(-1, 1, 2)
+    p = rng.uniform(0.5, 2.0)
+    return synth.prim_to_cons(rho, u, v, p)
+
+
+def test_eigenvectors_inverse_and_diagonalise_flux_jacobian():
+    """L R = I and R diag(lambda) L equals d(F n_x + G n_y)/dw (by complex step)."""
+    rng = np.random.default_rng(4)
+    g = 1.4
+    for _ in range(10):
+        w = _state(rng)
+        th = rng.uniform(0, 2 * np.pi)
+        nx, ny = np.cos(th), np.sin(th)
+        u, v, Hh, c = oracle.roe_average(w, w, g)
+        L, R = oracle.eigenvectors(u, v, Hh, c, nx, ny, g)
+        np.testing.assert_allclose(L @ R, np.eye(4), atol=1e-13)
+        qn = u * nx + v * ny
+        A = R @ np.diag([qn - c, qn, qn, qn + c]) @ L
+        J = np.zeros((4, 4))
+        for k in range(4):
+            wc = w.astype(complex)
+            wc[k] += 1e-30j
+            J[:, k] = H.normal_flux(wc, nx, ny, g).imag / 1e-30
+        np.testing.assert_allclose(A, J, atol=1e-12)
+
+
+def test_roe_average_satisfies_roe_property():
+    """F_n(w_R) - F_n(w_L) = A(w~)(w_R - w_L) with A = R Lambda L at the Roe state."""
+    rng = np.random.default_rng(6)
+    g = 1.4
+    for _ in range(10):
+        wl, wr = _state(rng), _state(rng)
+        nx, ny = 0.6, 0.8
+        u, v, Hh, c = oracle.roe_average(wl, wr, g)
+        L, R = oracle.eigenvectors(u, v, Hh, c, nx, ny, g)
+        qn = u * nx + v * ny
+        A = R @ np.diag([qn - c, qn, qn, qn + c]) @ L
+        np.testing.assert_allclose(A @ (wr - wl), H.normal_flux(wr, nx, ny, g)
+                                   - H.normal_flux(wl, nx, ny, g), atol=1e-12)
+
+
+def test_roe_flux_consistency_and_supersonic_upwinding():
+    rng = np.random.default_rng(8)
+    g = 1.4
+    w = _state(rng)
+    np.testing.assert_allclose(oracle.roe_flux(w, w, 0.6, 0.8, g), H.normal_flux(w, 0.6, 0.8, g),
+                               rtol=1e-15)
+    # supersonic to the right: every wave speed positive and above the entropy-fix width
+    wl = synth.prim_to_cons(1.0, 3.0, 0.1, 1.0)
+    wr = synth.prim_to_cons(1.1, 3.1, 0.0, 1.05)
+    np.testing.assert_allclose(oracle.roe_flux(wl, wr, 1.0, 0.0, g), H.normal_flux(wl, 1.0, 0.0, g),
+                               rtol=1e-13)
+
+
+# ------------------------------------------------------------------ LS divergence (Sec. 2.3)
+
+def test_divergence_rows_exact_for_degree5_fields(c1):
+    """Eq. (flux_polynomials): if f and g are polynomials of the fitted degree and h is their
+    projection at the edge midpoints, the rows return div f, div f_x and div f_y exactly."""
+    m, topo = c1
+    opts = oracle.Options()
+    rng = np.random.default_rng(2)
+    for v in rng.choice(len(m["x"]), 8, replace=False):
+        verts, edges, d, deg = oracle.div_rows(m, topo, int(v), opts)
+        assert deg == 5
+        a, b = rng.standard_normal(21), rng.standard_normal(21)
+
+        def val(c, r):
+            return oracle.taylor_basis(r[0], r[1], 5)[0] @ c
+        z = []
+        for u in verts:
+            r = H.disp(m, int(v), int(u))
+            z += [val(a, r), val(b, r)]
+        for e in edges:
+            t, hd = topo["edges"][e]
+            dd = H.disp(m, int(t), int(hd))
+            r = H.disp(m, int(v), int(t)) + 0.5 * dd
+            n = dd / np.linalg.norm(dd)
+            z.append(val(a, r) * n[0] + val(b, r) * n[1])
+        got = d @ np.array(z)
+        want = [a[1] + b[2], a[3] + b[4], a[4] + b[5]]      # f_x+g_y, f_xx+g_xy, f_xy+g_yy
+        np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-9 * np.abs(want).max())
+
+
+def test_viscous_rows_exact_for_quartics(c1):
+    m, topo = c1
+    opts = oracle.Options()
+    rng = np.random.default_rng(12)
+    for v in rng.choice(len(m["x"]), 5, replace=False):
+        verts, rows = oracle.visc_rows(m, topo, int(v), opts)
+        a, b = rng.standard_normal(15), rng.standard_normal(15)
+        z = []
+        for u in verts:
+            r = H.disp(m, int(v), int(u))
+            p = oracle.taylor_basis(r[0], r[1], 4)[0]
+            z += [p @ a, p @ b]
+        np.testing.assert_allclose(rows @ np.array(z), [a[1] + b[2], a[3] + b[4], a[4] + b[5]],
+                                   rtol=1e-9, atol=1e-9)
+
+
+# ------------------------------------------------------------------ whole residual
+
+def test_freestream_preserved_periodic(c1, c1_prep):
+    m, _ = c1
+    U = synth.uniform_state(m)
+    R = oracle.residual(m, c1_prep, U)
+    F, _ = oracle.euler_flux(U[:4], 1.4)
+    assert np.abs(R).max() < 1e-12 * np.abs(F).max() / 0.25
+
+
+def test_freestream_preserved_with_ghosts():
+    m = synth.jittered_box_with_ghosts(12, 10, (0.0, 1.0), (0.0, 0.8), 5, seed=2)
+    P = oracle.prepare(m)
+    U = synth.uniform_state(m)
+    U[:, m["ghost_ids"]] = 123.0                    # overwritten by the ghost refresh
+    R = oracle.residual(m, P, U)
+    assert np.abs(R).max() < 1e-11
+    assert np.all(R[:, m["ghost_ids"]] == 0.0)
+
+
+def test_ghost_refresh_copies_donor_and_zeroes_normal_derivative():
+    m = synth.jittered_box_with_ghosts(8, 8, (0.0, 1.0), (0.0, 1.0), 3, seed=2)
+    U = np.random.default_rng(0).standard_normal((12, len(m["x"])))
+    oracle.ghost_fill(m, U)
+    for gid, d, f in zip(m["ghost_ids"], m["ghost_donor"], m["ghost_flags"]):
+        np.testing.assert_array_equal(U[0:4, gid], U[0:4, d])
+        np.testing.assert_array_equal(U[4:8, gid], 0.0 if f & 1 else U[4:8, d])
+        np.testing.assert_array_equal(U[8:12, gid], 0.0 if f & 2 else U[8:12, d])
+
+
+def test_residual_is_rotation_covariant():
+    """Rotating mesh and state by 90 degrees rotates the residual (stencil choices depend only
+    on angles and ids, which rotation keeps).  Catches swapped x/y rows, wrong signs and
+    transposed coefficient indices anywhere in the residual."""
+    n, L = 16, 4.0
+    m = synth.jittered_grid(n, n, L, L, seed=21)
+    U = synth.isentropic_vortex(m, center=(2.0, 2.0), beta=3.0)
+    mr = dict(m)
+    mr["x"], mr["y"] = (L - m["y"]) % L, m["x"].copy()
+    Ur = np.empty_like(U)
+
+    def rot(w):                                      # (rho, m, n, E) -> (rho, -n, m, E)
+        return np.stack([w[0], -w[2], w[1], w[3]])
+    Ur[0:4] = rot(U[0:4])
+    Ur[4:8] = rot(-U[8:12])                          # d/dx' = -d/dy
+    Ur[8:12] = rot(U[4:8])                           # d/dy' = d/dx
+    act = np.arange(0, n * n, 7)
+    P = oracle.prepare(m, active=act)
+    Pr = oracle.prepare(mr, active=act)
+    np.testing.assert_array_equal(P.stencil, Pr.stencil)
+    R = oracle.residual(m, P, U)
+    Rr = oracle.residual(mr, Pr, Ur)
+    want = np.concatenate([rot(R[0:4]), rot(-R[8:12]), rot(R[4:8])])
+    scale = np.abs(R).max()
+    np.testing.assert_allclose(Rr[:, act], want[:, act], atol=1e-10 * scale)
+
+
+def test_vortex_truncation_error_converges():
+    """Residual of the exact isentropic vortex against its exact time derivative
+    dw/dt = -(w_x + w_y) (advection by the mean flow (1, 1)): the error must fall at high
+    order under refinement (the paper reports about fifth order for the solution, Sec. 3.1)."""
+    errs = []
+    for n in (20, 40, 80):
+        m = synth.jittered_grid(n, n, 10.0, 10.0, seed=1)
+        U = synth.isentropic_vortex(m)
+        xy = np.stack([m["x"], m["y"]], 1)
+        act = np.nonzero((np.abs(xy[:, 0] - 5) < 2.0) & (np.abs(xy[:, 1] - 5) < 2.0))[0]
+        act = act[:: max(1, len(act) // 40)]
+        P = oracle.prepare(m, active=act)
+        R = oracle.residual(m, P, U)
+        errs.append(np.mean(np.abs(R[:4, act] + U[4:8, act] + U[8:12, act])))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders.min() > 2.5, (errs, orders)
+
+
+def test_ssp_rk3_is_third_order():
+    lam = -1.3 + 0.4j
+    errs = []
+    for nsteps in (20, 40, 80):
+        dt = 1.0 / nsteps
+        y = np.array([1.0 + 0j])
+        for _ in range(nsteps):
+            y = oracle.ssp_rk3(y, dt, lambda u: lam * u)
+        errs.append(abs(y[0] - np.exp(lam)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - 3.0) < 0.1), orders
+
+
+def test_viscous_flux_closed_forms():
+    """Couette-type shear u = a y with linear temperature: tau_xy = mu a, q = -kappa grad T."""
+    opts = oracle.Options(viscous=True, mu=0.1, prandtl=0.72, R_gas=1.0)
+    g = 1.4
+    a, rho, T0, Ty = 0.5, 1.3, 2.0, 0.25
+    y = 0.4
+    u = a * y
+    p = rho * opts.R_gas * (T0 + Ty * y)
+    w = synth.prim_to_cons(rho, u, 0.0, p)
+    py = rho * opts.R_gas * Ty
+    wy = np.array([0.0, rho * a, 0.0, py / (g - 1.0) + rho * u * a])
+    U = np.concatenate([w, np.zeros(4), wy])[:, None]
+    Fv, Gv = oracle.viscous_flux(U, opts)
+    kappa = opts.mu * g * opts.R_gas / (g - 1.0) / opts.prandtl
+    np.testing.assert_allclose(Fv[:, 0], [0, 0, opts.mu * a, 0.0], atol=1e-14)
+    np.testing.assert_allclose(Gv[:, 0], [0, opts.mu * a, 0, u * opts.mu * a + kappa * Ty],
+                               atol=1e-14)
+
+
+def test_viscous_divergence_of_taylor_green_is_laplacian():
+    """For the divergence-free Taylor-Green field with rho = 1, div tau = mu lap u = -2 mu u."""
+    n = 32
+    m = synth.jittered_grid(n, n, 2 * np.pi, 2 * np.pi, seed=3)
+    mu = 0.05
+    opts = oracle.Options(viscous=True, mu=mu, R_gas=1.0)
+    act = np.arange(0, n * n, 11)
+    P = oracle.prepare(m, opts, active=act)
+    U = synth.taylor_green(m)
+    Fv, Gv = oracle.viscous_flux(U, opts)
+    V = len(m["x"])
+    z = np.zeros(2 * V)
+    for q, want in ((1, -2 * mu * U[1]), (2, -2 * mu * U[2])):
+        z[0::2], z[1::2] = Fv[q], Gv[q]
+        got = P.Dv[0] @ z
+        assert np.abs(got - want[act]).max() < 2e-3 * mu
+
+
+def test_vertex_areas_tile_the_domain(c1):
+    m, _ = c1
+    A = oracle.vertex_areas(m)
+    assert abs(A.sum() - 100.0) < 1e-10
+    assert A.min() > 0
+
+
+def test_roe_flux_equals_exact_godunov_flux_for_a_single_shock():
+    """For Riemann data joined by one shock (Rankine-Hugoniot), the exact solution at x/t = 0
+    is the upwind state, and Roe's flux is exact there.  Pins the Riemann flux against the exact
+    Riemann solution (Toro's solver, tests/exact_riemann.py)."""
+    from exact_riemann import sample
+    g = 1.4
+    rho1, p1, u1 = 1.0, 1.0, 0.0
+    for M in (1.5, 2.5):                               # right-running shock into state 1
+        c1 = np.sqrt(g * p1 / rho1)
+        p2 = p1 * (1 + 2 * g / (g + 1) * (M * M - 1))
+        rho2 = rho1 * (g + 1) * M * M / ((g - 1) * M * M + 2)
+        s = M * c1
+        u2 = s * (1 - rho1 / rho2)
+        left, right = (rho2, u2, p2), (rho1, u1, p1)
+        r, u, p = sample(left, right, np.array([0.0]), g)[:, 0]
+        want = H.normal_flux(synth.prim_to_cons(r, u, 0.0, p), 1.0, 0.0, g)
+        got = oracle.roe_flux(synth.prim_to_cons(rho2, u2, 0.0, p2),
+                              synth.prim_to_cons(rho1, u1, 0.0, p1), 1.0, 0.0, g)
+        np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-12)
+
+
+def test_linearised_residual_has_growing_modes():
+    """Records a property of the method as read here: about a uniform state the Jacobian of
+    the residual (5-node branch everywhere) has eigenvalues with positive real part of order
+    1/h, driven by the derivative equations of Eq. (HWENO) evolved with the second
+    derivatives of the least-squares fit.  Time integration therefore amplifies round-off."""
+    n = 8
+    m = synth.jittered_grid(n, n, 1.0, 1.0, seed=3)
+    P = oracle.prepare(m)
+    U0 = synth.uniform_state(m, rho=1.0, u=0.5, v=0.2, p=1.0)
+    R0 = oracle.residual(m, P, U0.copy())
+    N = U0.size
+    J = np.zeros((N, N))
+    eps = 1e-7
+    for k in range(N):
+        U = U0.copy().ravel()
+        U[k] += eps
+        J[:, k] = (oracle.residual(m, P, U.reshape(12, -1)) - R0).ravel() / eps
+    growth = np.linalg.eigvals(J).real.max() / n
+    assert growth > 0.05
