@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the SSP-RK3 step of the Hermite finite-difference method on one GB300.
+
+Workload (default): the 2D four-quadrant Riemann problem on a 1024 x 1024 jittered, randomly
+split triangulation of the unit square with 5 transmissive ghost layers (1,048,576 physical
+vertices, 1,069,156 stored, ~3.2 M flux edges), device CFL time step (CFL 0.3).  Synthetic
+seeded inputs (synth/), no dataset.
+
+Metric: vertex-stage updates per second = physical vertices x 3 RK stages x steps / time.
+The primary line is the FP64 path; the FP32-bulk path is timed in the same run and reported
+under "variants".  Per-kernel times come from CUDA events around every launch in a second pass
+of the same steps (hfd_steps_profiled); the roofline object describes the dominant kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--n 1024]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this comparison) on a bounded
+patch of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "vertex-stage updates/s"
+FP64_NOMINAL_FLOPS = 1.25e12     # GB300 FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x ~2.07 GHz
+CPU_PATCH_N = 32                 # bounded oracle sample: 32 x 32 patch of the same workload
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    mesh = synth.jittered_box_with_ghosts(n, n, (0.0, 1.0), (0.0, 1.0), 5, seed=2)
+    return mesh, synth.four_quadrant(mesh)
+
+
+def workload_name(n):
+    return f"four-quadrant Riemann, {n}x{n} jittered random-split mesh, 5 ghost layers"
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline bookkeeping
+def algorithmic_costs(stats, T):
+    """Algorithmic bytes and FP64/FP32 flops of one launch of each kernel (one RK stage), from
+    the mesh's actual sizes.  T = bytes of the bulk type.  Per-unit figures:
+      vertex : 96 B state read + 12T AoS copy + 8T fluxes written, ~30 flop  per vertex
+      edge   : 24 B stencil + 2T normal + 48T weights + 4T flux written     per flux edge,
+               + 12T state copy read once per vertex; ~1530 flop per edge (smooth branch)
+      div    : 8 B row pointers + (4 B + 6T) per stencil vertex + (4 B + 3T) per stencil edge
+               + 96 B stage state + 96 B base state (2 of 3 stages) + 96 B written per vertex,
+               + 8T fluxes per vertex and 4T per edge read once; 48 flop per stencil vertex,
+               24 per stencil edge, 48 for the stage update."""
+    V, A, Ef = stats["nv"], stats["nactive"], stats["nflux_edges"]
+    nv, ne = stats["div_nv_total"], stats["div_ne_total"]
+    return {
+        "vertex": {"bytes": V * (96 + 20 * T), "flops": 30 * V},
+        "edge": {"bytes": Ef * (24 + 54 * T) + V * 12 * T, "flops": 1530 * Ef},
+        "div": {"bytes": A * (8 + 96 * (1 + 2.0 / 3.0) + 96) + nv * (4 + 6 * T) + ne * (4 + 3 * T)
+                + V * 8 * T + Ef * 4 * T, "flops": 48 * nv + 24 * ne + 48 * A},
+        "ghost": {"bytes": (V - A) * (12 + 96 + 96), "flops": 0},
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def time_oracle(seconds=12.0, steps=None, warmup=0):
+    """Times the FP64 oracle's SSP-RK3 step on a bounded patch of the workload; returns
+    (vertex-stage/s, effective cores, sample description, per-step seconds list)."""
+    import oracle
+    mesh, U = workload(CPU_PATCH_N)
+    P = oracle.prepare(mesh)
+    A = len(P.active)
+    dt = 0.5 * oracle.cfl_dt(mesh, P, U)
+    for _ in range(warmup):
+        U = oracle.step(mesh, P, U, dt)
+    times = []
+    c0, w0 = time.process_time(), time.perf_counter()
+    while True:
+        t = time.perf_counter()
+        U = oracle.step(mesh, P, U, dt)
+        times.append(time.perf_counter() - t)
+        if steps is not None and len(times) >= steps:
+            break
+        if steps is None and time.perf_counter() - w0 > seconds:
+            break
+    cores = (time.process_time() - c0) / max(time.perf_counter() - w0, 1e-9)
+    value = A * 3 * len(times) / sum(times)
+    sample = (f"oracle SSP-RK3 steps on a {CPU_PATCH_N}x{CPU_PATCH_N} patch of the same workload "
+              f"({A} physical vertices, 5 ghost layers), {len(times)} steps")
+    return value, max(1, round(cores)), sample, times
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    value, cores, sample, times = time_oracle(steps=args.steps, warmup=args.warmup)
+    ms = 1000.0 * sum(times) / len(times)
+    line = {
+        "metric": METRIC, "value": value, "unit": "vertex-stage/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": workload_name(CPU_PATCH_N) + " (bounded CPU sample)",
+                   "precision": "fp64", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "vertex-stage/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "vertex-stage/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ native arm
+def run_native(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2109_01286_gb300 import Prep
+    mesh, U = workload(args.n)
+    t0 = time.perf_counter()
+    prep = Prep(mesh)
+    prep_s = time.perf_counter() - t0
+    U_dev = torch.from_numpy(U).cuda()
+    stream = torch.cuda.current_stream()
+    results = {}
+    clocks_main = None
+    peak_hbm, peak_src = load_peaks()
+    for prec in ("fp64", "fp32"):
+        dm = prep.upload(prec)
+        st = dm.stats_dict()
+        Ui = dm.import_state(U_dev)
+        W = Ui.clone()
+        dm.steps(W, 0.0, args.warmup)
+        torch.cuda.synchronize()
+        X = Ui.clone()
+        barrier()
+        clk = Clocks(local) if prec == "fp64" else None
+        if clk:
+            clk.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        dm.steps(X, 0.0, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        if clk:
+            clocks_main = clk.stop()
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        finite = True
+        try:
+            dm.check()
+        except Exception:
+            finite = False
+        A = st["nactive"]
+        value = world * A * 3 * args.steps / (ms / 1000.0)
+        # second pass: the same steps launched kernel by kernel with events
+        Y = Ui.clone()
+        kms, nl = dm.steps_profiled(Y, 0.0, args.steps)
+        T = 8 if prec == "fp64" else 4
+        costs = algorithmic_costs(st, T)
+        launches_per_kind = {"vertex": 3 * args.steps, "edge": 3 * args.steps,
+                             "div": 3 * args.steps, "ghost": 4 * args.steps}
+        kern = {}
+        for k in ("vertex", "edge", "div", "ghost"):
+            n = launches_per_kind[k]
+            avg_s = kms[k] / 1000.0 / n
+            kern[k] = {"ms_total": kms[k], "launches": n, "avg_ms": 1000 * avg_s,
+                       "share": kms[k] / max(sum(kms.values()), 1e-12),
+                       "gbs": costs[k]["bytes"] / avg_s / 1e9,
+                       "tflops": costs[k]["flops"] / avg_s / 1e12}
+        results[prec] = {"ms": ms, "value": value, "finite": finite, "kernels": kern,
+                         "profiled_ms": sum(kms.values()), "launches": nl, "stats": st}
+        if prec == "fp64":
+            e2e = None
+            if not args.no_e2e:
+                hin = torch.from_numpy(U.copy()).pin_memory()
+                hout = torch.empty_like(hin).pin_memory()
+                dm.steps_host(hin, hout, 0.0, 1)         # warm the e2e buffers and graph
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    dm.steps_host(hin, hout, 0.0, 1)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                barrier()
+                ems = max_over_ranks(e0.elapsed_time(e1))
+                nbytes = hin.numel() * 8
+                e2e = {"value": world * A * 3 * args.steps / (ems / 1000.0), "unit": "vertex-stage/s",
+                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                       "ms_per_step": ems / args.steps}
+            results[prec]["e2e"] = e2e
+        del dm
+        torch.cuda.empty_cache()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    r = results["fp64"]
+    dom = max(r["kernels"], key=lambda k: r["kernels"][k]["share"])
+    kd = r["kernels"][dom]
+    roof = {"kernel": f"k_{dom}<double>", "bound": "alu", "achieved": kd["tflops"],
+            "peak": FP64_NOMINAL_FLOPS / 1e12, "unit": "TFLOP/s",
+            "frac": kd["tflops"] / (FP64_NOMINAL_FLOPS / 1e12), "traffic": None,
+            "peak_source": "nominal GB300 FP64 (MEASURED_PEAKS.json has no FP64 figure)",
+            "hbm_gbs": kd["gbs"], "hbm_frac": kd["gbs"] / peak_hbm,
+            "hbm_peak_source": peak_src}
+    f32 = results["fp32"]
+    dom32 = max(f32["kernels"], key=lambda k: f32["kernels"][k]["share"])
+    k32 = f32["kernels"][dom32]
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": "vertex-stage/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args.n), "precision": "fp64",
+                   "physical_vertices": r["stats"]["nactive"], "stored_vertices": r["stats"]["nv"],
+                   "flux_edges": r["stats"]["nflux_edges"], "time_step": "device CFL 0.3",
+                   "l2": "no flush: per-stage working set (state, coefficients) is several GB, "
+                         "far larger than the 129 MB L2",
+                   "parallelism": f"replicas x{world}", "prep_seconds": prep_s},
+        "roofline": roof,
+        "kernels_fp64": r["kernels"],
+        "variants": {"fp32_bulk": {
+            "value": f32["value"], "ms_per_step": f32["ms"] / args.steps, "dtype": "f32",
+            "state_finite": f32["finite"],
+            "roofline": {"kernel": f"k_{dom32}<float>", "bound": "hbm", "achieved": k32["gbs"],
+                         "peak": peak_hbm, "unit": "GB/s", "frac": k32["gbs"] / peak_hbm,
+                         "traffic": None, "peak_source": peak_src},
+            "kernels": f32["kernels"]}},
+        "state_finite": r["finite"],
+        "gpu_launches": int(r["launches"]),
+        "e2e": r.get("e2e"),
+        "clocks": clocks_main,
+    }
+    if args.gpus == 1 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample, _ = time_oracle()
+        line["cpu_baseline"] = {"value": v, "unit": "vertex-stage/s", "cores": cores,
+                                "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

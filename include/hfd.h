@@ -1,0 +1,194 @@
+/*
+ * hfd.h - C ABI of the GB300 Hermite finite-difference library.
+ *
+ * The library advances the semi-discrete system of the Hermite finite-difference method for
+ * 2D Euler / Navier-Stokes on unstructured triangle meshes (Zhou, Zhen, Qu, Cai, arXiv
+ * 2109.01286).  Each vertex carries 12 unknowns, w = (rho, rho u, rho v, E) and its
+ * derivatives w_x, w_y (Eq. (HWENO), Sec. 2.3).  One right-hand-side evaluation is three
+ * GPU kernels: analytic vertex fluxes (Sec. 2.3), Hermite-WENO interpolation plus a Riemann
+ * flux at every edge midpoint (Alg. 1, Eq. (2d_hweno_intp)), and the two-level least-squares
+ * divergence (Eq. (flux_polynomials) and the d_0/d_x/d_y rows), fused with the update of the
+ * three-stage TVD Runge-Kutta scheme (Sec. 2.3, end).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: HFD_OK or an hfd_status error code; no C++ exception crosses the ABI.  The
+ *    message of the last error of the calling thread is hfd_last_error().
+ *  - State arrays are 12 x V float64 structure-of-arrays (row r of vertex v at U[r*V + v]):
+ *    rows 0-3 w, rows 4-7 w_x, rows 8-11 w_y.  Arrays passed to hfd_residual / hfd_step /
+ *    hfd_steps are DEVICE pointers in the mesh's INTERNAL vertex order (space-filling-curve
+ *    order, non-ghost vertices first).  hfd_state_import / hfd_state_export convert from / to
+ *    the caller's input vertex order on the device.
+ *  - Device calls are asynchronous on the given stream (0 = legacy default stream) unless the
+ *    entry point says otherwise.  A mesh is not thread-safe: calls on one mesh must be
+ *    serialised by the caller.  Distinct meshes are independent.
+ *  - Pointers are caller-owned unless stated; the library copies what it keeps.
+ */
+#ifndef HFD_H
+#define HFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HFD_OK = 0,
+  HFD_ERR_ARG = 1,         /* invalid argument (null pointer, size, option out of range)   */
+  HFD_ERR_MESH = 2,        /* invalid mesh (bad triangle, index out of range, non-manifold) */
+  HFD_ERR_STENCIL = 3,     /* an edge stencil cannot be assembled (Sec. 2.1)               */
+  HFD_ERR_SINGULAR = 4,    /* a least-squares system has no usable singular value          */
+  HFD_ERR_CUDA = 5,        /* CUDA runtime error (message carries cudaGetErrorString)      */
+  HFD_ERR_NONFINITE = 6,   /* device error word: non-finite value produced                 */
+  HFD_ERR_POSITIVITY = 7,  /* device error word: rho <= 0 or p <= 0 after an RK stage       */
+  HFD_ERR_TIMEOUT = 8,     /* device error word: a bounded device wait gave up             */
+  HFD_ERR_UNSUPPORTED = 9  /* option combination not built                                 */
+} hfd_status;
+
+/* Mesh description (Sec. 2.1 works on the edges of a triangulation).  Host pointers, copied. */
+typedef struct {
+  int32_t nv;              /* number of vertices (ghosts included)                          */
+  int32_t ntri;            /* number of triangles                                           */
+  const double* x;         /* nv vertex coordinates                                         */
+  const double* y;
+  const int32_t* tri;      /* 3*ntri vertex ids, counter-clockwise                          */
+  double Lx, Ly;           /* domain extents; used for the minimum image on periodic axes   */
+  int32_t periodic_x;      /* nonzero: displacements along x wrap with period Lx            */
+  int32_t periodic_y;
+  int32_t nghost;          /* transmissive ghost vertices (no residual, refreshed by copy)  */
+  const int32_t* ghost_ids;    /* nghost ids                                                */
+  const int32_t* ghost_donor;  /* nghost donor ids (non-ghost vertices)                     */
+  const int32_t* ghost_flags;  /* bit 0: zero w_x on refresh, bit 1: zero w_y               */
+} hfd_mesh_desc;
+
+/* Numerical options.  hfd_default_options fills the defaults shown. */
+typedef struct {
+  int32_t precision;       /* 0: FP64 throughout; 1: FP32 bulk (FP64 state, RK accumulation,
+                              geometry solves, WENO weight ratios)                        [0] */
+  int32_t div_degree;      /* degree of the LS divergence polynomials                     [5] */
+  int32_t visc_degree;     /* degree of the viscous vertex-only LS                        [4] */
+  int32_t viscous;         /* nonzero: add the viscous flux divergence                    [0] */
+  int32_t renumber;        /* nonzero: internal order along a Hilbert curve               [1] */
+  int32_t nthreads;        /* host preprocessing threads, 0 = all hardware threads        [0] */
+  double gamma;            /* ratio of specific heats                                   [1.4] */
+  double mu;               /* dynamic viscosity (constant)                                [0] */
+  double prandtl;          /* Prandtl number                                           [0.72] */
+  double R_gas;            /* gas constant, p = rho R T                                   [1] */
+  double weno_eps;         /* epsilon of the WENO weights                              [1e-2] */
+  double sens_lo;          /* smooth (5-node) branch iff sens_lo < omega_1 < sens_hi   [0.01] */
+  double sens_hi;          /*                                                          [0.79] */
+  double sv_rtol;          /* singular values <= sv_rtol*sigma_max count as zero      [1e-13] */
+  double div_cond_min;     /* LS degree drops by one below this sigma ratio estimate  [1e-12] */
+  double harten;           /* entropy-fix width as a fraction of the Roe sound speed    [0.1] */
+  double cfl;              /* CFL number of the device time step                        [0.3] */
+} hfd_options;
+
+typedef struct {
+  int64_t nv;              /* vertices                                                      */
+  int64_t nactive;         /* non-ghost vertices (residual rows), internal ids [0, nactive) */
+  int64_t nedges;          /* edges of the triangulation                                    */
+  int64_t nflux_edges;     /* edges whose numerical flux some divergence row reads          */
+  int64_t div_nnz;         /* total divergence row length (2N+M summed over active)         */
+  int64_t div_nv_total;    /* total stencil vertices N summed over active vertices          */
+  int64_t div_ne_total;    /* total stencil edges M summed over active vertices             */
+  int32_t div_nv_max, div_ne_max;
+  int64_t rank_hist[16];   /* 5-node ranks kept, over both sides of every flux edge         */
+  int64_t div_degree_fallbacks;
+  int64_t device_bytes;    /* device memory held by the mesh                                */
+  double prep_seconds;     /* host preprocessing wall time                                  */
+} hfd_mesh_stats;
+
+typedef struct hfd_prep hfd_prep;
+typedef struct hfd_mesh hfd_mesh;
+
+void hfd_default_options(hfd_options* opts);
+const char* hfd_last_error(void);
+
+/* ---------------------------------------------------------------- host preprocessing
+ * hfd_prep_create runs the geometry-only preprocessing on the host in FP64 (no GPU needed):
+ * edge list (Sec. 2.1), curvilinear 6-node stencils of every edge a divergence row reads
+ * (Sec. 2.1, Fig. 1; extension by smallest deflection, ties to the lower input id), the
+ * 5-node Hermite weights (first row of the pseudo-inverse of the 15x15 system of
+ * Eq. (hintp_5), Sec. 2.2, with trial dropping of singular values), the 3-node weights of
+ * Eq. (3nodes_intp), and the divergence rows d_0, d_x, d_y of Eq. (flux_polynomials) for every
+ * non-ghost vertex (plus the viscous vertex-only rows if opts->viscous).
+ * Errors: HFD_ERR_ARG, HFD_ERR_MESH, HFD_ERR_STENCIL, HFD_ERR_SINGULAR. */
+hfd_status hfd_prep_create(const hfd_mesh_desc* desc, const hfd_options* opts, hfd_prep** out);
+void hfd_prep_destroy(hfd_prep* prep);
+
+/* Named arrays of a prep object, all in INPUT numbering.  hfd_prep_size returns the element
+ * count of `name` (or -1); hfd_prep_get copies it out; hfd_prep_set overwrites it (same size;
+ * only the coefficient arrays "w5", "w3", "div_coef", "visc_coef" are writable).  Names:
+ *   "edges" int32 [E][2] (tail < head, sorted); "flux_edges" int32 [Ef] edge indices;
+ *   "stencil" int32 [Ef][6]; "normal" f64 [Ef][2]; "w5" f64 [Ef][2][15] (side, node*3 +
+ *   {value, x, y}); "w3" f64 [Ef][2][3][3] (side, sub-stencil, node); "rank" int32 [Ef][2];
+ *   "active" int32 [A]; "div_vptr" int32 [A+1]; "div_vidx" int32; "div_eptr" int32 [A+1];
+ *   "div_eidx" int32 (edge indices); "div_coef" f64, per active vertex a block of
+ *   3 x (2N+M) (rows d_0, d_x, d_y over the data [f_1, g_1, ..., f_N, g_N, h_1..h_M]);
+ *   "div_degree" int32 [A]; "visc_coef" f64, per active vertex 3 x 2N. */
+int64_t hfd_prep_size(const hfd_prep* prep, const char* name);
+hfd_status hfd_prep_get(const hfd_prep* prep, const char* name, void* dst, int64_t count);
+hfd_status hfd_prep_set(hfd_prep* prep, const char* name, const void* src, int64_t count);
+
+/* ---------------------------------------------------------------- device mesh
+ * hfd_mesh_create = hfd_prep_create + hfd_mesh_upload.  hfd_mesh_upload renumbers vertices
+ * and edges (Hilbert order of coordinates; non-ghost vertices first) and uploads the
+ * structure-of-arrays coefficient streams in the requested precision to the current device.
+ * The prep object is not consumed.  Errors: as hfd_prep_create, HFD_ERR_CUDA. */
+hfd_status hfd_mesh_create(const hfd_mesh_desc* desc, const hfd_options* opts, hfd_mesh** out);
+/* precision: -1 = the prep's option, 0 = FP64, 1 = FP32 bulk (one prep can feed both). */
+hfd_status hfd_mesh_upload(const hfd_prep* prep, int32_t precision, hfd_mesh** out);
+void hfd_mesh_destroy(hfd_mesh* mesh);
+hfd_status hfd_mesh_info(const hfd_mesh* mesh, hfd_mesh_stats* out);
+/* perm[internal id] = input vertex id (host array of nv entries). */
+hfd_status hfd_mesh_perm(const hfd_mesh* mesh, int32_t* perm);
+
+/* Device permutation of 12 x V state arrays between input order and internal order. */
+hfd_status hfd_state_import(hfd_mesh* mesh, const double* U_input, double* U_internal,
+                            void* stream);
+hfd_status hfd_state_export(hfd_mesh* mesh, const double* U_internal, double* U_input,
+                            void* stream);
+
+/* Right-hand side R(U) of Eq. (HWENO): rows 0-3 -div f, rows 4-7 -div f_x, rows 8-11 -div f_y
+ * (plus the viscous divergences), zero at ghost vertices.  The ghost columns of U are refreshed
+ * in place first (transmissive copy from the donor, flagged derivatives zeroed).  U and R are
+ * 12*nv device arrays in internal order and must not overlap. */
+hfd_status hfd_residual(hfd_mesh* mesh, double* U, double* R, void* stream);
+
+/* One step of the three-stage TVD Runge-Kutta scheme (Sec. 2.3), in place on U:
+ * u1 = u + dt R(u); u2 = 3/4 u + 1/4 (u1 + dt R(u1)); u <- 1/3 u + 2/3 (u2 + dt R(u2)).
+ * Only non-ghost vertices advance; ghost columns are refreshed at the end.  dt > 0 is used as
+ * given; dt <= 0 selects dt = cfl * min_v l_min(v) / (|u| + c) computed on the device from
+ * the step's initial state (no host synchronisation). */
+hfd_status hfd_step(hfd_mesh* mesh, double* U, double dt, void* stream);
+
+/* nsteps calls of hfd_step, replayed from a CUDA graph captured on the first call for this
+ * (U, dt mode).  Same semantics as nsteps calls of hfd_step. */
+hfd_status hfd_steps(hfd_mesh* mesh, double* U, double dt, int32_t nsteps, void* stream);
+
+/* End-to-end form with HOST buffers in input order: copies U_in (12*nv doubles, ideally
+ * pinned) to the device, imports it, runs nsteps steps, exports and copies the result to
+ * U_out (may equal U_in), then synchronises the stream.  Uses mesh-owned device buffers. */
+hfd_status hfd_steps_host(hfd_mesh* mesh, const double* U_in, double* U_out, double dt,
+                          int32_t nsteps, void* stream);
+
+/* Same work as hfd_steps, launched kernel by kernel with CUDA events recorded around each
+ * launch on `stream`; synchronises the stream and accumulates into kernel_ms[5] the time spent
+ * in each kernel kind: [0] ghost refresh, [1] vertex fluxes, [2] edge interpolation + Riemann
+ * flux, [3] divergence + RK stage, [4] time-step reduction.  Returns the launch count in
+ * *launches.  Tracing aid: the events add a few microseconds per launch. */
+hfd_status hfd_steps_profiled(hfd_mesh* mesh, double* U, double dt, int32_t nsteps, void* stream,
+                              double* kernel_ms, int64_t* launches);
+
+/* dt used by the most recent step (synchronises the stream). */
+hfd_status hfd_last_dt(hfd_mesh* mesh, double* dt, void* stream);
+
+/* Reads and clears the device error word (synchronises the stream): HFD_OK if clean, else the
+ * first recorded error (HFD_ERR_NONFINITE, HFD_ERR_POSITIVITY). */
+hfd_status hfd_check(hfd_mesh* mesh, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFD_H */

@@ -1,0 +1,10 @@
+"""GB300-native Hermite finite-difference residual and SSP-RK3 step (arXiv 2109.01286).
+
+`hfd` is the Python binding of the C ABI declared in include/hfd.h; the computation runs in the
+in-tree library `_lib/libhfd.so` (host C++ preprocessing + CUDA kernels for sm_103a), built by
+`build.build()`.
+"""
+from . import hfd
+from .hfd import HfdError, Mesh, Prep, options
+
+__all__ = ["hfd", "HfdError", "Mesh", "Prep", "options"]

@@ -1,0 +1,516 @@
+// C ABI of the device mesh: renumbering, upload of the coefficient streams, residual, SSP-RK3
+// steps (direct launches or a replayed CUDA graph), end-to-end host form, error word.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "kernels.hpp"
+#include "prep.hpp"
+
+using hfd::DevMesh;
+using hfd::Phys;
+using hfd::set_error;
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct hfd_mesh {
+  hfd_options opts{};
+  DevMesh dm;
+  Phys ph{};
+  int lanes = 8;
+  std::vector<int32_t> perm;            // internal -> input
+  int32_t* dperm = nullptr;             // device copy of perm
+  double* U1 = nullptr;                 // stage buffers 12 x V
+  double* U2 = nullptr;
+  double* Uin = nullptr;                // end-to-end staging (input order)
+  double* Uint = nullptr;               // end-to-end staging (internal order)
+  cudaStream_t cap = nullptr;           // private stream used for graph capture
+  std::map<std::pair<const double*, double>, GraphEntry> graphs;
+  hfd_mesh_stats stats{};
+  std::vector<void*> allocs;
+  int device = 0;
+};
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      set_error("%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return HFD_ERR_CUDA;                                                         \
+    }                                                                              \
+  } while (0)
+
+namespace {
+
+// Hilbert index of (x, y) in [0, 2^16)^2 (the classic rotate-and-flip construction).
+uint64_t hilbert(uint32_t x, uint32_t y) {
+  uint64_t d = 0;
+  for (uint32_t s = 1u << 15; s > 0; s >>= 1) {
+    uint32_t rx = (x & s) ? 1 : 0, ry = (y & s) ? 1 : 0;
+    d += (uint64_t)s * s * ((3 * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) { x = s - 1 - x; y = s - 1 - y; }
+      std::swap(x, y);
+    }
+  }
+  return d;
+}
+
+template <typename T>
+hfd_status dev_upload(hfd_mesh* m, void** dst, const std::vector<T>& src) {
+  size_t bytes = std::max<size_t>(src.size() * sizeof(T), 16);
+  void* p = nullptr;
+  CK(cudaMalloc(&p, bytes));
+  m->allocs.push_back(p);
+  m->stats.device_bytes += (int64_t)bytes;
+  if (!src.empty()) CK(cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *dst = p;
+  return HFD_OK;
+}
+
+hfd_status dev_alloc(hfd_mesh* m, void** dst, size_t bytes) {
+  void* p = nullptr;
+  bytes = std::max<size_t>(bytes, 16);
+  CK(cudaMalloc(&p, bytes));
+  CK(cudaMemset(p, 0, bytes));
+  m->allocs.push_back(p);
+  m->stats.device_bytes += (int64_t)bytes;
+  *dst = p;
+  return HFD_OK;
+}
+
+#define TRY(x)                       \
+  do {                               \
+    hfd_status s_ = (x);             \
+    if (s_ != HFD_OK) return s_;     \
+  } while (0)
+
+// Upload the coefficient streams in bulk precision T.
+template <typename T>
+hfd_status upload_streams(hfd_mesh* m, const hfd::Prep& P, const std::vector<int32_t>& inv,
+                          const std::vector<int32_t>& fint /* prep flux index -> internal */,
+                          const std::vector<int32_t>& fperm /* internal -> prep flux index */,
+                          const std::vector<int32_t>& emap /* edge -> internal flux id */) {
+  DevMesh& d = m->dm;
+  const int Ef = d.Ef, A = d.A;
+  std::vector<int32_t> sten((size_t)6 * Ef);
+  std::vector<T> nrm((size_t)2 * Ef), w5((size_t)30 * Ef), w3((size_t)18 * Ef);
+  for (int fi = 0; fi < Ef; ++fi) {
+    int f = fperm[fi];
+    for (int k = 0; k < 6; ++k) sten[(size_t)k * Ef + fi] = inv[P.stencil[6 * (size_t)f + k]];
+    nrm[fi] = (T)P.normal[2 * (size_t)f];
+    nrm[(size_t)Ef + fi] = (T)P.normal[2 * (size_t)f + 1];
+    for (int k = 0; k < 30; ++k) w5[(size_t)k * Ef + fi] = (T)P.w5[30 * (size_t)f + k];
+    for (int k = 0; k < 18; ++k) w3[(size_t)k * Ef + fi] = (T)P.w3[18 * (size_t)f + k];
+  }
+  (void)fint;
+  TRY(dev_upload(m, (void**)&d.sten, sten));
+  TRY(dev_upload(m, &d.nrm, nrm));
+  TRY(dev_upload(m, &d.w5, w5));
+  TRY(dev_upload(m, &d.w3, w3));
+  // divergence CSR in internal vertex order
+  std::vector<int32_t> arow(P.nv, -1);
+  for (size_t r = 0; r < P.active.size(); ++r) arow[P.active[r]] = (int32_t)r;
+  std::vector<int32_t> vptr(A + 1, 0), eptr(A + 1, 0);
+  for (int ri = 0; ri < A; ++ri) {
+    int r = arow[m->perm[ri]];
+    vptr[ri + 1] = vptr[ri] + (P.div_vptr[r + 1] - P.div_vptr[r]);
+    eptr[ri + 1] = eptr[ri] + (P.div_eptr[r + 1] - P.div_eptr[r]);
+  }
+  std::vector<int32_t> vidx(vptr[A]), eidx(eptr[A]);
+  std::vector<T> cv((size_t)6 * vptr[A]), ce((size_t)3 * eptr[A]), cvis;
+  if (P.opts.viscous) cvis.resize((size_t)6 * vptr[A]);
+  for (int ri = 0; ri < A; ++ri) {
+    int r = arow[m->perm[ri]];
+    int N = P.div_vptr[r + 1] - P.div_vptr[r], M = P.div_eptr[r + 1] - P.div_eptr[r];
+    int L = 2 * N + M;
+    const double* c = &P.div_coef[P.div_cptr[r]];
+    T* cvb = &cv[(size_t)6 * vptr[ri]];
+    T* ceb = &ce[(size_t)3 * eptr[ri]];
+    for (int j = 0; j < N; ++j) {
+      vidx[vptr[ri] + j] = inv[P.div_vidx[P.div_vptr[r] + j]];
+      for (int row = 0; row < 3; ++row) {
+        cvb[(2 * row) * N + j] = (T)c[row * L + 2 * j];
+        cvb[(2 * row + 1) * N + j] = (T)c[row * L + 2 * j + 1];
+      }
+    }
+    for (int j = 0; j < M; ++j) {
+      eidx[eptr[ri] + j] = emap[P.div_eidx[P.div_eptr[r] + j]];
+      for (int row = 0; row < 3; ++row) ceb[row * M + j] = (T)c[row * L + 2 * N + j];
+    }
+    if (P.opts.viscous) {
+      const double* z = &P.visc_coef[P.visc_cptr[r]];
+      T* cz = &cvis[(size_t)6 * vptr[ri]];
+      for (int j = 0; j < N; ++j)
+        for (int row = 0; row < 3; ++row) {
+          cz[(2 * row) * N + j] = (T)z[row * 2 * N + 2 * j];
+          cz[(2 * row + 1) * N + j] = (T)z[row * 2 * N + 2 * j + 1];
+        }
+    }
+  }
+  TRY(dev_upload(m, (void**)&d.vptr, vptr));
+  TRY(dev_upload(m, (void**)&d.eptr, eptr));
+  TRY(dev_upload(m, (void**)&d.vidx, vidx));
+  TRY(dev_upload(m, (void**)&d.eidx, eidx));
+  TRY(dev_upload(m, &d.cv, cv));
+  TRY(dev_upload(m, &d.ce, ce));
+  if (P.opts.viscous) TRY(dev_upload(m, &d.cvis, cvis));
+  const size_t V = d.V;
+  TRY(dev_alloc(m, &d.Ua, V * 12 * sizeof(T)));
+  TRY(dev_alloc(m, &d.FG, V * 8 * sizeof(T)));
+  if (P.opts.viscous) TRY(dev_alloc(m, &d.FGv, V * 8 * sizeof(T)));
+  TRY(dev_alloc(m, &d.h, (size_t)Ef * 4 * sizeof(T)));
+  m->stats.div_nnz = vptr[A] * 2 + eptr[A];
+  return HFD_OK;
+}
+
+hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
+  CK(cudaGetDevice(&m->device));
+  m->opts = P.opts;
+  if (precision >= 0) m->opts.precision = precision;
+  DevMesh& d = m->dm;
+  const int V = P.nv;
+  const int A = (int)P.active.size();
+  d.V = V;
+  d.A = A;
+  d.G = (int)P.ghost_ids.size();
+  d.Ef = (int)P.flux_edges.size();
+  d.precision = m->opts.precision;
+  d.viscous = P.opts.viscous;
+  // ---- vertex order: non-ghosts first, each part along a Hilbert curve
+  m->perm.resize(V);
+  {
+    double x0 = 0, x1 = P.Lx, y0 = 0, y1 = P.Ly;
+    if (!P.periodic_x || !(x1 > 0)) {
+      x0 = *std::min_element(P.x.begin(), P.x.end());
+      x1 = *std::max_element(P.x.begin(), P.x.end());
+    }
+    if (!P.periodic_y || !(y1 > 0)) {
+      y0 = *std::min_element(P.y.begin(), P.y.end());
+      y1 = *std::max_element(P.y.begin(), P.y.end());
+    }
+    double sx = x1 > x0 ? 65535.0 / (x1 - x0) : 0, sy = y1 > y0 ? 65535.0 / (y1 - y0) : 0;
+    std::vector<uint64_t> key(V);
+    for (int v = 0; v < V; ++v) {
+      double xn = (P.x[v] - x0) * sx, yn = (P.y[v] - y0) * sy;
+      uint32_t xi = (uint32_t)std::min(65535.0, std::max(0.0, xn));
+      uint32_t yi = (uint32_t)std::min(65535.0, std::max(0.0, yn));
+      key[v] = P.opts.renumber ? hilbert(xi, yi) : 0;
+    }
+    std::iota(m->perm.begin(), m->perm.end(), 0);
+    std::stable_sort(m->perm.begin(), m->perm.end(), [&](int a, int b) {
+      if (P.is_ghost[a] != P.is_ghost[b]) return P.is_ghost[a] < P.is_ghost[b];
+      if (key[a] != key[b]) return key[a] < key[b];
+      return a < b;
+    });
+  }
+  std::vector<int32_t> inv(V);
+  for (int i = 0; i < V; ++i) inv[m->perm[i]] = i;
+  // ---- flux edge order: by internal (min, max) end ids
+  const int Ef = d.Ef;
+  std::vector<int32_t> fperm(Ef);
+  std::iota(fperm.begin(), fperm.end(), 0);
+  auto ekey = [&](int f) {
+    int e = P.flux_edges[f];
+    int a = inv[P.edges[2 * (size_t)e]], b = inv[P.edges[2 * (size_t)e + 1]];
+    return std::make_pair(std::min(a, b), std::max(a, b));
+  };
+  std::sort(fperm.begin(), fperm.end(), [&](int a, int b) { return ekey(a) < ekey(b); });
+  std::vector<int32_t> fint(Ef), emap(P.nedges(), -1);
+  for (int i = 0; i < Ef; ++i) {
+    fint[fperm[i]] = i;
+    emap[P.flux_edges[fperm[i]]] = i;
+  }
+  hfd_status st = d.precision == 0 ? upload_streams<double>(m, P, inv, fint, fperm, emap)
+                                   : upload_streams<float>(m, P, inv, fint, fperm, emap);
+  if (st != HFD_OK) return st;
+  // ---- ghosts, time-step data, perm, stage buffers, scalars
+  std::vector<int32_t> gid(d.G), gdn(d.G), gfl(d.G);
+  for (int g = 0; g < d.G; ++g) {
+    gid[g] = inv[P.ghost_ids[g]];
+    gdn[g] = inv[P.ghost_donor[g]];
+    gfl[g] = P.ghost_flags[g];
+  }
+  TRY(dev_upload(m, (void**)&d.gid, gid));
+  TRY(dev_upload(m, (void**)&d.gdonor, gdn));
+  TRY(dev_upload(m, (void**)&d.gflags, gfl));
+  std::vector<double> lmin(A);
+  for (int i = 0; i < A; ++i) lmin[i] = P.lmin[m->perm[i]];
+  TRY(dev_upload(m, (void**)&d.lmin, lmin));
+  TRY(dev_upload(m, (void**)&m->dperm, m->perm));
+  TRY(dev_alloc(m, (void**)&d.dtbits, sizeof(unsigned long long)));
+  TRY(dev_alloc(m, (void**)&d.dt_last, sizeof(double)));
+  TRY(dev_alloc(m, (void**)&d.err, sizeof(unsigned)));
+  TRY(dev_alloc(m, (void**)&m->U1, (size_t)12 * V * sizeof(double)));
+  TRY(dev_alloc(m, (void**)&m->U2, (size_t)12 * V * sizeof(double)));
+  CK(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+  const hfd_options& o = P.opts;
+  m->ph.gamma = o.gamma;
+  m->ph.eps = o.weno_eps;
+  m->ph.sens_lo = o.sens_lo;
+  m->ph.sens_hi = o.sens_hi;
+  m->ph.harten = o.harten;
+  m->ph.cfl = o.cfl;
+  m->ph.mu = o.mu;
+  m->ph.R_gas = o.R_gas;
+  m->ph.kappa = o.mu * (o.gamma * o.R_gas / (o.gamma - 1.0)) / o.prandtl;
+  // ---- stats
+  hfd_mesh_stats& s = m->stats;
+  s.nv = V;
+  s.nactive = A;
+  s.nedges = P.nedges();
+  s.nflux_edges = Ef;
+  s.div_nv_total = P.div_vptr.empty() ? 0 : P.div_vptr.back();
+  s.div_ne_total = P.div_eptr.empty() ? 0 : P.div_eptr.back();
+  for (int r = 0; r < A; ++r) {
+    s.div_nv_max = std::max(s.div_nv_max, P.div_vptr[r + 1] - P.div_vptr[r]);
+    s.div_ne_max = std::max(s.div_ne_max, P.div_eptr[r + 1] - P.div_eptr[r]);
+  }
+  for (int32_t r : P.rank) s.rank_hist[std::min(15, std::max(0, r))]++;
+  s.div_degree_fallbacks = P.degree_fallbacks;
+  s.prep_seconds = P.prep_seconds;
+  return HFD_OK;
+}
+
+hfd_status residual_impl(hfd_mesh* m, double* U, double* R, cudaStream_t s) {
+  CK(hfd::launch_ghost(m->dm, U, s));
+  CK(hfd::launch_vertex(m->dm, U, m->ph, s));
+  CK(hfd::launch_edge(m->dm, m->ph, s));
+  CK(hfd::launch_div(m->dm, U, U, R, hfd::DIV_RESIDUAL, 0.0, 1.0, 1.0, m->ph, m->lanes, s));
+  const DevMesh& d = m->dm;
+  if (d.V > d.A)
+    CK(cudaMemset2DAsync(R + d.A, (size_t)d.V * sizeof(double), 0,
+                         (size_t)(d.V - d.A) * sizeof(double), 12, s));
+  return HFD_OK;
+}
+
+// Optional per-kernel timing of the launches of a step (hfd_steps_profiled).
+struct Timer {
+  cudaStream_t s;
+  double ms[5] = {0, 0, 0, 0, 0};
+  int64_t launches = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+};
+
+// One SSP-RK3 step: three stages of (ghost refresh, vertex fluxes, edge fluxes, divergence +
+// stage combination), plus the device time step and a final ghost refresh.
+hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* tm = nullptr) {
+  const DevMesh& d = m->dm;
+  auto timed = [&](int kind, auto&& launch) -> cudaError_t {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (tm) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, s);
+    }
+    cudaError_t e = launch();
+    if (tm) {
+      cudaEventRecord(b, s);
+      tm->ev.push_back({kind, {a, b}});
+      tm->launches++;
+    }
+    return e;
+  };
+  if (!(dt > 0.0)) CK(timed(4, [&] { return hfd::launch_dtmin(d, U, m->ph, s); }));
+  static const double A_[3] = {0.0, 0.75, 1.0 / 3.0}, B_[3] = {1.0, 0.25, 2.0 / 3.0};
+  double* in[3] = {U, m->U1, m->U2};
+  double* out[3] = {m->U1, m->U2, U};
+  for (int k = 0; k < 3; ++k) {
+    if (d.G) CK(timed(0, [&] { return hfd::launch_ghost(d, in[k], s); }));
+    CK(timed(1, [&] { return hfd::launch_vertex(d, in[k], m->ph, s); }));
+    CK(timed(2, [&] { return hfd::launch_edge(d, m->ph, s); }));
+    CK(timed(3, [&] {
+      return hfd::launch_div(d, in[k], U, out[k], hfd::DIV_STAGE, A_[k], B_[k], dt, m->ph,
+                             m->lanes, s);
+    }));
+  }
+  if (d.G) CK(timed(0, [&] { return hfd::launch_ghost(d, U, s); }));
+  return HFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hfd_status hfd_mesh_upload(const hfd_prep* prep, int32_t precision, hfd_mesh** out) {
+  if (!prep || !out || precision < -1 || precision > 1) {
+    set_error("hfd_mesh_upload: invalid argument");
+    return HFD_ERR_ARG;
+  }
+  *out = nullptr;
+  hfd_mesh* m = new (std::nothrow) hfd_mesh();
+  if (!m) { set_error("hfd_mesh_upload: out of host memory"); return HFD_ERR_ARG; }
+  hfd_status st;
+  try {
+    st = upload(*prep, precision, m);
+  } catch (const std::exception& e) {
+    set_error("hfd_mesh_upload: %s", e.what());
+    st = HFD_ERR_ARG;
+  }
+  if (st != HFD_OK) { hfd_mesh_destroy(m); return st; }
+  *out = m;
+  return HFD_OK;
+}
+
+hfd_status hfd_mesh_create(const hfd_mesh_desc* desc, const hfd_options* opts, hfd_mesh** out) {
+  hfd_prep* p = nullptr;
+  hfd_status st = hfd_prep_create(desc, opts, &p);
+  if (st != HFD_OK) return st;
+  st = hfd_mesh_upload(p, -1, out);
+  hfd_prep_destroy(p);
+  return st;
+}
+
+void hfd_mesh_destroy(hfd_mesh* m) {
+  if (!m) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(m->device);
+  for (auto& kv : m->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (m->cap) cudaStreamDestroy(m->cap);
+  for (void* p : m->allocs) cudaFree(p);
+  cudaSetDevice(prev);
+  delete m;
+}
+
+hfd_status hfd_mesh_info(const hfd_mesh* m, hfd_mesh_stats* out) {
+  if (!m || !out) { set_error("hfd_mesh_info: null argument"); return HFD_ERR_ARG; }
+  *out = m->stats;
+  return HFD_OK;
+}
+
+hfd_status hfd_mesh_perm(const hfd_mesh* m, int32_t* perm) {
+  if (!m || !perm) { set_error("hfd_mesh_perm: null argument"); return HFD_ERR_ARG; }
+  std::memcpy(perm, m->perm.data(), m->perm.size() * sizeof(int32_t));
+  return HFD_OK;
+}
+
+hfd_status hfd_state_import(hfd_mesh* m, const double* Uin, double* Uint, void* stream) {
+  if (!m || !Uin || !Uint) { set_error("hfd_state_import: null argument"); return HFD_ERR_ARG; }
+  CK(hfd::launch_permute(m->dm.V, m->dperm, Uin, Uint, true, (cudaStream_t)stream));
+  return HFD_OK;
+}
+
+hfd_status hfd_state_export(hfd_mesh* m, const double* Uint, double* Uin, void* stream) {
+  if (!m || !Uin || !Uint) { set_error("hfd_state_export: null argument"); return HFD_ERR_ARG; }
+  CK(hfd::launch_permute(m->dm.V, m->dperm, Uint, Uin, false, (cudaStream_t)stream));
+  return HFD_OK;
+}
+
+hfd_status hfd_residual(hfd_mesh* m, double* U, double* R, void* stream) {
+  if (!m || !U || !R || U == R) { set_error("hfd_residual: invalid argument"); return HFD_ERR_ARG; }
+  return residual_impl(m, U, R, (cudaStream_t)stream);
+}
+
+hfd_status hfd_step(hfd_mesh* m, double* U, double dt, void* stream) {
+  if (!m || !U) { set_error("hfd_step: invalid argument"); return HFD_ERR_ARG; }
+  return step_impl(m, U, dt, (cudaStream_t)stream);
+}
+
+hfd_status hfd_steps(hfd_mesh* m, double* U, double dt, int32_t nsteps, void* stream) {
+  if (!m || !U || nsteps < 0) { set_error("hfd_steps: invalid argument"); return HFD_ERR_ARG; }
+  if (nsteps == 0) return HFD_OK;
+  auto key = std::make_pair((const double*)U, dt > 0.0 ? dt : 0.0);
+  GraphEntry& g = m->graphs[key];
+  if (!g.exec) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal));
+    hfd_status st = step_impl(m, U, dt, m->cap);
+    cudaError_t ce = cudaStreamEndCapture(m->cap, &graph);
+    if (st != HFD_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      m->graphs.erase(key);
+      return st;
+    }
+    if (ce != cudaSuccess) {
+      m->graphs.erase(key);
+      set_error("hfd_steps: capture failed: %s", cudaGetErrorString(ce));
+      return HFD_ERR_CUDA;
+    }
+    ce = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      m->graphs.erase(key);
+      set_error("hfd_steps: instantiate failed: %s", cudaGetErrorString(ce));
+      return HFD_ERR_CUDA;
+    }
+  }
+  for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(g.exec, (cudaStream_t)stream));
+  return HFD_OK;
+}
+
+hfd_status hfd_steps_profiled(hfd_mesh* m, double* U, double dt, int32_t nsteps, void* stream,
+                              double* kernel_ms, int64_t* launches) {
+  if (!m || !U || nsteps < 0 || !kernel_ms) {
+    set_error("hfd_steps_profiled: invalid argument");
+    return HFD_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Timer tm;
+  tm.s = s;
+  hfd_status st = HFD_OK;
+  for (int i = 0; i < nsteps && st == HFD_OK; ++i) st = step_impl(m, U, dt, s, &tm);
+  cudaError_t e = cudaStreamSynchronize(s);
+  for (auto& x : tm.ev) {
+    float ms = 0;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, x.second.first, x.second.second);
+    kernel_ms[x.first] += ms;
+    cudaEventDestroy(x.second.first);
+    cudaEventDestroy(x.second.second);
+  }
+  if (launches) *launches = tm.launches;
+  if (st != HFD_OK) return st;
+  CK(e);
+  return HFD_OK;
+}
+
+hfd_status hfd_steps_host(hfd_mesh* m, const double* U_in, double* U_out, double dt,
+                          int32_t nsteps, void* stream) {
+  if (!m || !U_in || !U_out || nsteps < 0) {
+    set_error("hfd_steps_host: invalid argument");
+    return HFD_ERR_ARG;
+  }
+  size_t bytes = (size_t)12 * m->dm.V * sizeof(double);
+  if (!m->Uin) {
+    TRY(dev_alloc(m, (void**)&m->Uin, bytes));
+    TRY(dev_alloc(m, (void**)&m->Uint, bytes));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(m->Uin, U_in, bytes, cudaMemcpyHostToDevice, s));
+  CK(hfd::launch_permute(m->dm.V, m->dperm, m->Uin, m->Uint, true, s));
+  TRY(hfd_steps(m, m->Uint, dt, nsteps, stream));
+  CK(hfd::launch_permute(m->dm.V, m->dperm, m->Uint, m->Uin, false, s));
+  CK(cudaMemcpyAsync(U_out, m->Uin, bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return HFD_OK;
+}
+
+hfd_status hfd_last_dt(hfd_mesh* m, double* dt, void* stream) {
+  if (!m || !dt) { set_error("hfd_last_dt: null argument"); return HFD_ERR_ARG; }
+  CK(cudaMemcpyAsync(dt, m->dm.dt_last, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return HFD_OK;
+}
+
+hfd_status hfd_check(hfd_mesh* m, void* stream) {
+  if (!m) { set_error("hfd_check: null argument"); return HFD_ERR_ARG; }
+  unsigned w = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(&w, m->dm.err, sizeof w, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemsetAsync(m->dm.err, 0, sizeof(unsigned), s));
+  CK(cudaStreamSynchronize(s));
+  if (w & 1u) { set_error("device error word: non-finite value"); return HFD_ERR_NONFINITE; }
+  if (w & 2u) { set_error("device error word: rho <= 0 after a stage"); return HFD_ERR_POSITIVITY; }
+  return HFD_OK;
+}
+
+}  // extern "C"

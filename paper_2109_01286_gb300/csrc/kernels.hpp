@@ -1,0 +1,64 @@
+// Device mesh layout and kernel launchers (kernels.cu), used by the C ABI (api.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace hfd {
+
+// Physical and numerical constants passed by value to the kernels.
+struct Phys {
+  double gamma, eps, sens_lo, sens_hi, harten, cfl;
+  double mu, kappa, R_gas;      // viscous model (Sec. 2.3; constant mu, kappa = mu c_p / Pr)
+};
+
+// Device arrays of one mesh in internal numbering.  Coefficient and flux arrays hold elements
+// of the path's bulk precision T (double or float), addressed through void pointers here.
+struct DevMesh {
+  int V = 0;        // vertices; internal ids [0, A) are non-ghost, [A, V) ghosts
+  int A = 0;
+  int Ef = 0;       // flux edges
+  int G = 0;        // ghost vertices
+  int precision = 0;
+  int viscous = 0;
+  // edge streams: stencil [6][Ef] (internal vertex ids), normal [2][Ef], 5-node weights
+  // [30][Ef] (side L 15, side R 15; node*3 + {value, x, y}), 3-node weights [18][Ef]
+  int32_t* sten = nullptr;
+  void* nrm = nullptr;
+  void* w5 = nullptr;
+  void* w3 = nullptr;
+  // divergence CSR over active vertices; per-vertex SoA coefficient blocks:
+  // cv at 6*vptr[r]: d0F, d0G, dxF, dxG, dyF, dyG (each N long); ce at 3*eptr[r]: d0, dx, dy
+  int32_t *vptr = nullptr, *vidx = nullptr, *eptr = nullptr, *eidx = nullptr;
+  void* cv = nullptr;
+  void* ce = nullptr;
+  void* cvis = nullptr;  // viscous rows, same layout as cv
+  // ghosts
+  int32_t *gid = nullptr, *gdonor = nullptr, *gflags = nullptr;
+  // time step
+  double* lmin = nullptr;                 // [A] shortest incident edge
+  unsigned long long* dtbits = nullptr;   // min over vertices of lmin/(|u|+c), as bits
+  double* dt_last = nullptr;
+  unsigned* err = nullptr;                // device error word
+  // scratch: AoS copies of the state [V][12], vertex fluxes [V][8] (+ viscous), edge fluxes [Ef][4]
+  void* Ua = nullptr;
+  void* FG = nullptr;
+  void* FGv = nullptr;
+  void* h = nullptr;
+};
+
+enum DivMode { DIV_RESIDUAL = 0, DIV_STAGE = 1 };
+
+cudaError_t launch_ghost(const DevMesh& m, double* U, cudaStream_t s);
+cudaError_t launch_vertex(const DevMesh& m, const double* U, const Phys& ph, cudaStream_t s);
+cudaError_t launch_edge(const DevMesh& m, const Phys& ph, cudaStream_t s);
+// out = R (residual mode) or out = a*Un + b*(Us + dt*R) (stage mode); dt_fixed <= 0 selects
+// dt = cfl * (device minimum).
+cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, double* out,
+                       int mode, double a, double b, double dt_fixed, const Phys& ph,
+                       int lanes, cudaStream_t s);
+cudaError_t launch_dtmin(const DevMesh& m, const double* U, const Phys& ph, cudaStream_t s);
+cudaError_t launch_permute(int V, const int32_t* perm, const double* src, double* dst,
+                           bool gather, cudaStream_t s);
+
+}  // namespace hfd

@@ -1,0 +1,851 @@
+// Host preprocessing of the Hermite finite-difference method: everything geometry-only, in FP64,
+// computed once per mesh.  Paper: arXiv 2109.01286.
+//   * edge list and curvilinear 6-node stencils (Sec. 2.1, Fig. 1);
+//   * 5-node Hermite least-squares weights: first row of the pseudo-inverse of the 15x15 system
+//     of Eq. (hintp_5) (Sec. 2.2), by a one-sided Jacobi SVD with trial dropping of singular
+//     values;
+//   * 3-node Lagrangian weights of Eq. (3nodes_intp) (Sec. 2.3), min-norm, in double-double;
+//   * two-level least-squares divergence rows d_0, d_x, d_y of Eq. (flux_polynomials) and the
+//     viscous vertex-only rows (Sec. 2.3), by Householder QR with column pivoting.
+// Host code is compiled with -ffp-contract=off so that the geometric quantities that decide
+// discrete choices (stencil cosines) are evaluated exactly as written.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <thread>
+
+#include "prep.hpp"
+
+namespace hfd {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+const char* last_error() { return g_err; }
+
+// ------------------------------------------------------------------ small utilities
+
+template <class F>
+static void parallel_for(int64_t n, int nthreads, F f) {
+  if (nthreads <= 1 || n < 256) {
+    for (int64_t i = 0; i < n; ++i) f(i, 0);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  const int64_t chunk = 64;
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&, t] {
+      for (;;) {
+        int64_t s = next.fetch_add(chunk);
+        if (s >= n) break;
+        int64_t e = std::min(n, s + chunk);
+        for (int64_t i = s; i < e; ++i) f(i, t);
+      }
+    });
+  for (auto& x : th) x.join();
+}
+
+struct ErrorSlot {
+  std::mutex mu;
+  hfd_status st = HFD_OK;
+  char msg[512] = "";
+  void set(hfd_status s, const char* m) {
+    std::lock_guard<std::mutex> g(mu);
+    if (st == HFD_OK) {
+      st = s;
+      snprintf(msg, sizeof msg, "%s", m);
+    }
+  }
+};
+
+double Prep::dispx(int a, int b) const {
+  double d = x[b] - x[a];
+  if (periodic_x) d = d - Lx * std::rint(d / Lx);
+  return d;
+}
+double Prep::dispy(int a, int b) const {
+  double d = y[b] - y[a];
+  if (periodic_y) d = d - Ly * std::rint(d / Ly);
+  return d;
+}
+
+// Complete Taylor basis x^a y^b/(a! b!) ordered by degree, then by decreasing a (Sec. 2.2).
+static int nterms(int deg) { return (deg + 1) * (deg + 2) / 2; }
+
+static void taylor(double x, double y, int deg, double* p, double* px, double* py) {
+  double xp[8], yp[8], fact[8];
+  xp[0] = yp[0] = fact[0] = 1.0;
+  for (int k = 1; k <= deg; ++k) {
+    xp[k] = xp[k - 1] * x;
+    yp[k] = yp[k - 1] * y;
+    fact[k] = fact[k - 1] * k;
+  }
+  int i = 0;
+  for (int d = 0; d <= deg; ++d)
+    for (int b = 0; b <= d; ++b, ++i) {
+      int a = d - b;
+      p[i] = xp[a] * yp[b] / (fact[a] * fact[b]);
+      if (px) px[i] = a > 0 ? xp[a - 1] * yp[b] / (fact[a - 1] * fact[b]) : 0.0;
+      if (py) py[i] = b > 0 ? xp[a] * yp[b - 1] / (fact[a] * fact[b - 1]) : 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ one-sided Jacobi SVD
+// Hestenes' method on the columns of A (m x n, column-major): A V = U diag(s).  On return A
+// holds U diag(s) (columns sorted by decreasing s), V the right singular vectors.
+static void jacobi_svd(int m, int n, double* A, double* V, double* s) {
+  for (int i = 0; i < n * n; ++i) V[i] = 0.0;
+  for (int i = 0; i < n; ++i) V[i + i * n] = 1.0;
+  for (int sweep = 0; sweep < 80; ++sweep) {
+    bool rotated = false;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double al = 0, be = 0, ga = 0;
+        double* ap = A + (size_t)p * m;
+        double* aq = A + (size_t)q * m;
+        for (int i = 0; i < m; ++i) {
+          al += ap[i] * ap[i];
+          be += aq[i] * aq[i];
+          ga += ap[i] * aq[i];
+        }
+        if (al == 0.0 || be == 0.0) continue;
+        if (std::fabs(ga) <= 1e-16 * std::sqrt(al * be)) continue;
+        rotated = true;
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+        for (int i = 0; i < m; ++i) {
+          double u = ap[i], w = aq[i];
+          ap[i] = c * u - sn * w;
+          aq[i] = sn * u + c * w;
+        }
+        double* vp = V + (size_t)p * n;
+        double* vq = V + (size_t)q * n;
+        for (int i = 0; i < n; ++i) {
+          double u = vp[i], w = vq[i];
+          vp[i] = c * u - sn * w;
+          vq[i] = sn * u + c * w;
+        }
+      }
+    if (!rotated) break;
+  }
+  std::vector<int> ord(n);
+  for (int j = 0; j < n; ++j) {
+    double t = 0;
+    for (int i = 0; i < m; ++i) t += A[i + (size_t)j * m] * A[i + (size_t)j * m];
+    s[j] = std::sqrt(t);
+    ord[j] = j;
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return s[a] > s[b]; });
+  std::vector<double> A2((size_t)m * n), V2((size_t)n * n), s2(n);
+  for (int j = 0; j < n; ++j) {
+    std::memcpy(&A2[(size_t)j * m], A + (size_t)ord[j] * m, sizeof(double) * m);
+    std::memcpy(&V2[(size_t)j * n], V + (size_t)ord[j] * n, sizeof(double) * n);
+    s2[j] = s[ord[j]];
+  }
+  std::memcpy(A, A2.data(), sizeof(double) * m * n);
+  std::memcpy(V, V2.data(), sizeof(double) * n * n);
+  std::memcpy(s, s2.data(), sizeof(double) * n);
+}
+
+// ------------------------------------------------------------------ Householder QR (pivoted)
+// Rows of the pseudo-inverse of a full-column-rank A (m x n, column-major): for each target
+// pair (i1, i2) the row (e_i1 + e_i2)^T A^+ (i2 < 0: e_i1 only).  A P = Q R, so the row is
+// Q z with R^T z = P^T e.  Returns |R_nn| / |R_11| as the conditioning estimate.
+static double ls_rows(int m, int n, std::vector<double>& A, const int (*targets)[2], int ntarg,
+                      double* rows /* ntarg x m */) {
+  std::vector<int> perm(n);
+  for (int j = 0; j < n; ++j) perm[j] = j;
+  std::vector<double> beta(n, 0.0), v0s(n, 0.0);
+  auto col = [&](int j) { return &A[(size_t)j * m]; };
+  for (int k = 0; k < n; ++k) {
+    int best = k;
+    double bn = -1;
+    for (int j = k; j < n; ++j) {
+      double t = 0;
+      const double* c = col(j);
+      for (int i = k; i < m; ++i) t += c[i] * c[i];
+      if (t > bn) { bn = t; best = j; }
+    }
+    if (best != k) {
+      std::swap_ranges(col(k), col(k) + m, col(best));
+      std::swap(perm[k], perm[best]);
+    }
+    double* c = col(k);
+    double nx = std::sqrt(bn);
+    if (nx == 0.0) { beta[k] = 0.0; continue; }
+    double alpha = c[k] >= 0 ? -nx : nx;
+    double v0 = c[k] - alpha;
+    // v = (v0, c[k+1..m-1]); v^T v = 2 (nx^2 - alpha c[k])
+    double vtv = v0 * v0;
+    for (int i = k + 1; i < m; ++i) vtv += c[i] * c[i];
+    double b = 2.0 / vtv;
+    for (int j = k + 1; j < n; ++j) {
+      double* cj = col(j);
+      double dot = v0 * cj[k];
+      for (int i = k + 1; i < m; ++i) dot += c[i] * cj[i];
+      dot *= b;
+      cj[k] -= dot * v0;
+      for (int i = k + 1; i < m; ++i) cj[i] -= dot * c[i];
+    }
+    c[k] = alpha;          // R_kk; the reflector tail stays below the diagonal
+    beta[k] = b;
+    v0s[k] = v0;
+  }
+  double r11 = std::fabs(A[0]), rnn = std::fabs(A[(size_t)(n - 1) * m + (n - 1)]);
+  std::vector<double> f(n), z(n), yv(m);
+  for (int t = 0; t < ntarg; ++t) {
+    for (int k = 0; k < n; ++k) {
+      int j = perm[k];
+      f[k] = (j == targets[t][0] ? 1.0 : 0.0) + (j == targets[t][1] ? 1.0 : 0.0);
+    }
+    for (int k = 0; k < n; ++k) {           // R^T z = f (forward substitution)
+      double acc = f[k];
+      for (int i = 0; i < k; ++i) acc -= A[(size_t)k * m + i] * z[i];
+      z[k] = acc / A[(size_t)k * m + k];
+    }
+    for (int i = 0; i < m; ++i) yv[i] = i < n ? z[i] : 0.0;
+    for (int k = n - 1; k >= 0; --k) {      // y = H_0 ... H_{n-1} [z; 0]
+      const double* c = col(k);
+      double dot = v0s[k] * yv[k];
+      for (int i = k + 1; i < m; ++i) dot += c[i] * yv[i];
+      dot *= beta[k];
+      yv[k] -= dot * v0s[k];
+      for (int i = k + 1; i < m; ++i) yv[i] -= dot * c[i];
+    }
+    std::memcpy(rows + (size_t)t * m, yv.data(), sizeof(double) * m);
+  }
+  return rnn / r11;
+}
+
+// ------------------------------------------------------------------ double-double (Dekker)
+struct dd { double hi, lo; };
+static inline dd two_sum(double a, double b) {
+  double s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+static inline dd quick_two_sum(double a, double b) {
+  double s = a + b;
+  return {s, b - (s - a)};
+}
+static inline dd two_prod(double a, double b) {
+  double p = a * b;
+  return {p, std::fma(a, b, -p)};
+}
+static inline dd dd_add(dd x, dd y) {
+  dd s = two_sum(x.hi, y.hi), t = two_sum(x.lo, y.lo);
+  s.lo += t.hi;
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return quick_two_sum(s.hi, s.lo);
+}
+static inline dd dd_neg(dd x) { return {-x.hi, -x.lo}; }
+static inline dd dd_mul(dd x, dd y) {
+  dd p = two_prod(x.hi, y.hi);
+  p.lo += x.hi * y.lo + x.lo * y.hi;
+  return quick_two_sum(p.hi, p.lo);
+}
+static inline dd dd_from(double a) { return {a, 0.0}; }
+static inline dd dd_div(dd a, dd b) {          // long division, three quotient terms
+  double q1 = a.hi / b.hi;
+  dd r = dd_add(a, dd_neg(dd_mul(dd_from(q1), b)));
+  double q2 = r.hi / b.hi;
+  r = dd_add(r, dd_neg(dd_mul(dd_from(q2), b)));
+  double q3 = r.hi / b.hi;
+  dd q = quick_two_sum(q1, q2);
+  return dd_add(q, dd_from(q3));
+}
+
+// 3-node weights of Eq. (3nodes_intp) in unscaled midpoint-relative coordinates: A = [p_3(x_k)]
+// (3 x 6) has full row rank for distinct nodes, A^+ = A^T (A A^T)^-1, and its first row is
+// w = (A A^T)^-1 1 because A's first column is all ones.  A A^T is nearly singular for short
+// edges, so G and Cramer's rule are evaluated in double-double; the value weights are then
+// made to sum to one at node `near` (constant consistency) before the final rounding.
+static void three_node(const double (*rel)[2], int near, double* w) {
+  dd A[3][6];
+  for (int k = 0; k < 3; ++k) {
+    double x = rel[k][0], y = rel[k][1];
+    dd xx = two_prod(x, x), xy = two_prod(x, y), yy = two_prod(y, y);
+    A[k][0] = dd_from(1.0);
+    A[k][1] = dd_from(x);
+    A[k][2] = dd_from(y);
+    A[k][3] = {xx.hi * 0.5, xx.lo * 0.5};
+    A[k][4] = xy;
+    A[k][5] = {yy.hi * 0.5, yy.lo * 0.5};
+  }
+  dd G[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      dd s = dd_from(0.0);
+      for (int k = 0; k < 6; ++k) s = dd_add(s, dd_mul(A[i][k], A[j][k]));
+      G[i][j] = s;
+    }
+  auto det3 = [](dd M[3][3]) {
+    dd a = dd_add(dd_mul(M[1][1], M[2][2]), dd_neg(dd_mul(M[1][2], M[2][1])));
+    dd b = dd_add(dd_mul(M[1][0], M[2][2]), dd_neg(dd_mul(M[1][2], M[2][0])));
+    dd c = dd_add(dd_mul(M[1][0], M[2][1]), dd_neg(dd_mul(M[1][1], M[2][0])));
+    return dd_add(dd_add(dd_mul(M[0][0], a), dd_neg(dd_mul(M[0][1], b))), dd_mul(M[0][2], c));
+  };
+  dd den = det3(G);
+  dd num[3];
+  for (int c = 0; c < 3; ++c) {
+    dd M[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) M[i][j] = (j == c) ? dd_from(1.0) : G[i][j];
+    num[c] = det3(M);
+  }
+  dd sum = dd_add(dd_add(num[0], num[1]), num[2]);
+  num[near] = dd_add(num[near], dd_add(den, dd_neg(sum)));
+  for (int c = 0; c < 3; ++c) {
+    dd q = dd_div(num[c], den);
+    w[c] = q.hi + q.lo;
+  }
+}
+
+// 5-node Hermite weights (Sec. 2.2) for nodes rel[5] (relative to the edge midpoint), edge
+// length ell, near node index 2.  Scaled coordinates (x/ell): data (c, ell c_x, ell c_y).
+// Keep singular values > sv_rtol*sigma_max, then drop the smallest while any stored scaled
+// weight has magnitude >= 1.  Unscale derivative weights, fix value weights to sum to one.
+static int five_node(const double (*rel)[2], double ell, double sv_rtol, double* w) {
+  double P[15 * 15], V[15 * 15], s[15];
+  double p[15], px[15], py[15];
+  for (int j = 0; j < 5; ++j) {
+    taylor(rel[j][0] / ell, rel[j][1] / ell, 4, p, px, py);
+    for (int k = 0; k < 15; ++k) {            // row 3j (+1, +2), column-major storage
+      P[(3 * j) + 15 * k] = p[k];
+      P[(3 * j + 1) + 15 * k] = px[k];
+      P[(3 * j + 2) + 15 * k] = py[k];
+    }
+  }
+  jacobi_svd(15, 15, P, V, s);
+  int r = 0;
+  for (int i = 0; i < 15; ++i)
+    if (s[i] > sv_rtol * s[0]) ++r;
+  for (;;) {
+    double mx = 0;
+    for (int i = 0; i < 15; ++i) w[i] = 0.0;
+    for (int k = 0; k < r; ++k) {
+      double f = V[0 + 15 * k] / (s[k] * s[k]);   // V[0,k] U[:,k] / s_k, with U s = A V
+      for (int i = 0; i < 15; ++i) w[i] += f * P[i + 15 * k];
+    }
+    for (int i = 0; i < 15; ++i) mx = std::max(mx, std::fabs(w[i]));
+    if (mx < 1.0) break;
+    if (--r == 0) return 0;
+  }
+  double sum = 0;
+  for (int j = 0; j < 5; ++j) {
+    w[3 * j + 1] *= ell;
+    w[3 * j + 2] *= ell;
+  }
+  for (int j = 0; j < 5; ++j) sum += w[3 * j];
+  w[6] += 1.0 - sum;
+  return r;
+}
+
+// ------------------------------------------------------------------ build
+
+// One stencil extension (Sec. 2.1): neighbour of cur, not yet used, with the largest cosine
+// to the travel direction t; ties within 1e-12 keep the lower id (ascending scan).
+static int extend(const Prep& P, int cur, double tx, double ty, const int* used, int nused,
+                  double* dx, double* dy) {
+  double tn = std::sqrt(tx * tx + ty * ty);
+  int best = -1;
+  double bc = -INFINITY, bx = 0, by = 0;
+  for (int k = P.nbr_ptr[cur]; k < P.nbr_ptr[cur + 1]; ++k) {
+    int c = P.nbr_idx[k];
+    bool u = false;
+    for (int i = 0; i < nused; ++i) u |= (used[i] == c);
+    if (u) continue;
+    double ex = P.dispx(cur, c), ey = P.dispy(cur, c);
+    double cs = (tx * ex + ty * ey) / (tn * std::sqrt(ex * ex + ey * ey));
+    if (cs > bc + 1e-12) { best = c; bc = cs; bx = ex; by = ey; }
+  }
+  *dx = bx;
+  *dy = by;
+  return best;
+}
+
+hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!d || !o || !d->x || !d->y || !d->tri || d->nv <= 0 || d->ntri <= 0) {
+    set_error("hfd_prep_create: null pointer or empty mesh");
+    return HFD_ERR_ARG;
+  }
+  if (o->div_degree < 2 || o->div_degree > 6 || o->visc_degree < 2 || o->visc_degree > 6 ||
+      o->precision < 0 || o->precision > 1) {
+    set_error("hfd_prep_create: option out of range");
+    return HFD_ERR_ARG;
+  }
+  P->opts = *o;
+  const int nv = d->nv;
+  P->nv = nv;
+  P->x.assign(d->x, d->x + nv);
+  P->y.assign(d->y, d->y + nv);
+  P->tri.assign(d->tri, d->tri + 3 * (size_t)d->ntri);
+  P->Lx = d->Lx;
+  P->Ly = d->Ly;
+  P->periodic_x = d->periodic_x;
+  P->periodic_y = d->periodic_y;
+  if ((P->periodic_x && !(d->Lx > 0)) || (P->periodic_y && !(d->Ly > 0))) {
+    set_error("hfd_prep_create: periodic axis needs a positive period");
+    return HFD_ERR_ARG;
+  }
+  P->is_ghost.assign(nv, 0);
+  if (d->nghost > 0) {
+    if (!d->ghost_ids || !d->ghost_donor || !d->ghost_flags) {
+      set_error("hfd_prep_create: ghost arrays missing");
+      return HFD_ERR_ARG;
+    }
+    P->ghost_ids.assign(d->ghost_ids, d->ghost_ids + d->nghost);
+    P->ghost_donor.assign(d->ghost_donor, d->ghost_donor + d->nghost);
+    P->ghost_flags.assign(d->ghost_flags, d->ghost_flags + d->nghost);
+    for (int g = 0; g < d->nghost; ++g) {
+      int id = d->ghost_ids[g];
+      if (id < 0 || id >= nv || P->is_ghost[id]) {
+        set_error("hfd_prep_create: ghost id %d invalid or repeated", id);
+        return HFD_ERR_MESH;
+      }
+      P->is_ghost[id] = 1;
+    }
+    for (int g = 0; g < d->nghost; ++g) {
+      int dn = d->ghost_donor[g];
+      if (dn < 0 || dn >= nv || P->is_ghost[dn]) {
+        set_error("hfd_prep_create: ghost donor %d invalid (must be a non-ghost vertex)", dn);
+        return HFD_ERR_MESH;
+      }
+    }
+  }
+  // ---- edges
+  std::vector<uint64_t> keys;
+  keys.reserve(3 * (size_t)d->ntri);
+  for (int t = 0; t < d->ntri; ++t) {
+    const int* v = &P->tri[3 * (size_t)t];
+    for (int k = 0; k < 3; ++k) {
+      int a = v[k], b = v[(k + 1) % 3];
+      if (a < 0 || a >= nv || b < 0 || b >= nv || a == b) {
+        set_error("hfd_prep_create: triangle %d has an invalid vertex", t);
+        return HFD_ERR_MESH;
+      }
+      if (a > b) std::swap(a, b);
+      keys.push_back(((uint64_t)a << 32) | (uint32_t)b);
+    }
+  }
+  std::sort(keys.begin(), keys.end());
+  {
+    // manifold check: an edge may appear in at most two triangles
+    size_t run = 1;
+    for (size_t i = 1; i <= keys.size(); ++i) {
+      if (i < keys.size() && keys[i] == keys[i - 1]) { ++run; continue; }
+      if (run > 2) {
+        set_error("hfd_prep_create: edge (%u,%u) shared by %zu triangles",
+                  (unsigned)(keys[i - 1] >> 32), (unsigned)(keys[i - 1] & 0xffffffffu), run);
+        return HFD_ERR_MESH;
+      }
+      run = 1;
+    }
+  }
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  const int64_t E = (int64_t)keys.size();
+  P->edges.resize(2 * E);
+  std::vector<int32_t> deg(nv, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    int a = (int)(keys[e] >> 32), b = (int)(keys[e] & 0xffffffffu);
+    P->edges[2 * e] = a;
+    P->edges[2 * e + 1] = b;
+    deg[a]++;
+    deg[b]++;
+  }
+  P->nbr_ptr.assign(nv + 1, 0);
+  for (int v = 0; v < nv; ++v) P->nbr_ptr[v + 1] = P->nbr_ptr[v] + deg[v];
+  P->nbr_idx.resize(2 * E);
+  P->nbr_edge.resize(2 * E);
+  {
+    std::vector<int32_t> fill(P->nbr_ptr.begin(), P->nbr_ptr.end() - 1);
+    for (int64_t e = 0; e < E; ++e) {       // edges sorted by (a, b): lists come out sorted
+      int a = P->edges[2 * e], b = P->edges[2 * e + 1];
+      P->nbr_idx[fill[a]] = b;
+      P->nbr_edge[fill[a]++] = (int32_t)e;
+    }
+    for (int64_t e = 0; e < E; ++e) {
+      int a = P->edges[2 * e], b = P->edges[2 * e + 1];
+      P->nbr_idx[fill[b]] = a;
+      P->nbr_edge[fill[b]++] = (int32_t)e;
+    }
+    for (int v = 0; v < nv; ++v) {          // sort each list by neighbour id
+      int s = P->nbr_ptr[v], t = P->nbr_ptr[v + 1];
+      std::vector<std::pair<int, int>> tmp;
+      for (int k = s; k < t; ++k) tmp.push_back({P->nbr_idx[k], P->nbr_edge[k]});
+      std::sort(tmp.begin(), tmp.end());
+      for (int k = s; k < t; ++k) {
+        P->nbr_idx[k] = tmp[k - s].first;
+        P->nbr_edge[k] = tmp[k - s].second;
+      }
+    }
+  }
+  P->lmin.assign(nv, 0.0);
+  for (int v = 0; v < nv; ++v) {
+    double m = INFINITY;
+    for (int k = P->nbr_ptr[v]; k < P->nbr_ptr[v + 1]; ++k) {
+      double ex = P->dispx(v, P->nbr_idx[k]), ey = P->dispy(v, P->nbr_idx[k]);
+      m = std::min(m, std::sqrt(ex * ex + ey * ey));
+    }
+    P->lmin[v] = m;
+  }
+  int nthreads = o->nthreads > 0 ? o->nthreads : (int)std::max(1u, std::thread::hardware_concurrency());
+
+  // ---- two-level stencils of active vertices (Fig. 6: distance <= 2, edges inside the set)
+  for (int v = 0; v < nv; ++v)
+    if (!P->is_ghost[v]) P->active.push_back(v);
+  const int64_t A = (int64_t)P->active.size();
+  std::vector<std::vector<int32_t>> sv(A), se(A);
+  {
+    std::vector<std::vector<int32_t>> mark(nthreads, std::vector<int32_t>(nv, -1));
+    parallel_for(A, nthreads, [&](int64_t r, int t) {
+      int v = P->active[r];
+      auto& mk = mark[t];
+      std::vector<int32_t>& verts = sv[r];
+      verts.push_back(v);
+      mk[v] = (int)r;
+      for (int k = P->nbr_ptr[v]; k < P->nbr_ptr[v + 1]; ++k) {
+        int u = P->nbr_idx[k];
+        if (mk[u] != r) { mk[u] = (int)r; verts.push_back(u); }
+      }
+      size_t n1 = verts.size();
+      for (size_t i = 1; i < n1; ++i) {
+        int u = verts[i];
+        for (int k = P->nbr_ptr[u]; k < P->nbr_ptr[u + 1]; ++k) {
+          int w = P->nbr_idx[k];
+          if (mk[w] != r) { mk[w] = (int)r; verts.push_back(w); }
+        }
+      }
+      std::sort(verts.begin(), verts.end());
+      for (int u : verts)
+        for (int k = P->nbr_ptr[u]; k < P->nbr_ptr[u + 1]; ++k) {
+          int w = P->nbr_idx[k];
+          if (w > u && mk[w] == r) se[r].push_back(P->nbr_edge[k]);
+        }
+      std::sort(se[r].begin(), se[r].end());
+      for (int u : verts) mk[u] = -1;
+    });
+  }
+  P->div_vptr.assign(A + 1, 0);
+  P->div_eptr.assign(A + 1, 0);
+  P->div_cptr.assign(A + 1, 0);
+  for (int64_t r = 0; r < A; ++r) {
+    P->div_vptr[r + 1] = P->div_vptr[r] + (int)sv[r].size();
+    P->div_eptr[r + 1] = P->div_eptr[r] + (int)se[r].size();
+    P->div_cptr[r + 1] = P->div_cptr[r] + 3 * (int64_t)(2 * sv[r].size() + se[r].size());
+  }
+  P->div_vidx.resize(P->div_vptr[A]);
+  P->div_eidx.resize(P->div_eptr[A]);
+  P->div_coef.assign(P->div_cptr[A], 0.0);
+  P->div_degree.assign(A, 0);
+  if (o->viscous) {
+    P->visc_cptr.assign(A + 1, 0);
+    for (int64_t r = 0; r < A; ++r) P->visc_cptr[r + 1] = P->visc_cptr[r] + 6 * (int64_t)sv[r].size();
+    P->visc_coef.assign(P->visc_cptr[A], 0.0);
+  }
+  ErrorSlot err;
+  std::atomic<int64_t> fallbacks(0);
+  parallel_for(A, nthreads, [&](int64_t r, int) {
+    int v = P->active[r];
+    const auto& verts = sv[r];
+    const auto& eds = se[r];
+    std::copy(verts.begin(), verts.end(), P->div_vidx.begin() + P->div_vptr[r]);
+    std::copy(eds.begin(), eds.end(), P->div_eidx.begin() + P->div_eptr[r]);
+    int N = (int)verts.size(), M = (int)eds.size();
+    double ell = 0;
+    int nn = 0;
+    for (int k = P->nbr_ptr[v]; k < P->nbr_ptr[v + 1]; ++k, ++nn) {
+      double ex = P->dispx(v, P->nbr_idx[k]), ey = P->dispy(v, P->nbr_idx[k]);
+      ell += std::sqrt(ex * ex + ey * ey);
+    }
+    ell /= nn;
+    std::vector<double> xv(2 * N), xm(2 * M), nm(2 * M);
+    for (int j = 0; j < N; ++j) {
+      xv[2 * j] = P->dispx(v, verts[j]) / ell;
+      xv[2 * j + 1] = P->dispy(v, verts[j]) / ell;
+    }
+    for (int j = 0; j < M; ++j) {
+      int a = P->edges[2 * eds[j]], b = P->edges[2 * eds[j] + 1];
+      double ex = P->dispx(a, b), ey = P->dispy(a, b);
+      xm[2 * j] = (P->dispx(v, a) + 0.5 * ex) / ell;
+      xm[2 * j + 1] = (P->dispy(v, a) + 0.5 * ey) / ell;
+      double len = std::sqrt(ex * ex + ey * ey);
+      nm[2 * j] = ex / len;
+      nm[2 * j + 1] = ey / len;
+    }
+    int degv = o->div_degree;
+    int rows = 2 * N + M;
+    std::vector<double> out(3 * (size_t)rows);
+    double p[32];
+    for (;;) {
+      int K = nterms(degv), n = 2 * K;
+      if (rows < n) { --degv; if (degv < 1) break; continue; }
+      std::vector<double> Am((size_t)rows * n, 0.0);
+      for (int j = 0; j < N; ++j) {
+        taylor(xv[2 * j], xv[2 * j + 1], degv, p, nullptr, nullptr);
+        for (int k = 0; k < K; ++k) {
+          Am[(2 * j) + (size_t)k * rows] = p[k];
+          Am[(2 * j + 1) + (size_t)(K + k) * rows] = p[k];
+        }
+      }
+      for (int j = 0; j < M; ++j) {
+        taylor(xm[2 * j], xm[2 * j + 1], degv, p, nullptr, nullptr);
+        for (int k = 0; k < K; ++k) {
+          Am[(2 * N + j) + (size_t)k * rows] = p[k] * nm[2 * j];
+          Am[(2 * N + j) + (size_t)(K + k) * rows] = p[k] * nm[2 * j + 1];
+        }
+      }
+      const int targ[3][2] = {{1, K + 2}, {3, K + 4}, {4, K + 5}};
+      double cond = ls_rows(rows, n, Am, targ, 3, out.data());
+      if (cond >= o->div_cond_min || degv <= 2) break;
+      --degv;
+      fallbacks++;
+    }
+    P->div_degree[r] = degv;
+    double* c = &P->div_coef[P->div_cptr[r]];
+    for (int i = 0; i < rows; ++i) {
+      c[i] = out[i] / ell;
+      c[rows + i] = out[rows + i] / (ell * ell);
+      c[2 * rows + i] = out[2 * rows + i] / (ell * ell);
+    }
+    if (o->viscous) {                       // vertex-only LS, f and g decoupled (Sec. 2.3)
+      int K = nterms(o->visc_degree);
+      std::vector<double> B((size_t)N * K);
+      for (int j = 0; j < N; ++j) {
+        taylor(xv[2 * j], xv[2 * j + 1], o->visc_degree, p, nullptr, nullptr);
+        for (int k = 0; k < K; ++k) B[j + (size_t)k * N] = p[k];
+      }
+      if (N < K) {
+        err.set(HFD_ERR_SINGULAR, "viscous stencil has fewer vertices than basis terms");
+        return;
+      }
+      const int targ[5][2] = {{1, -1}, {2, -1}, {3, -1}, {4, -1}, {5, -1}};
+      std::vector<double> q(5 * (size_t)N);
+      ls_rows(N, K, B, targ, 5, q.data());
+      double* e = &P->visc_coef[P->visc_cptr[r]];
+      double l2 = ell * ell;
+      for (int j = 0; j < N; ++j) {           // rows over interleaved (f_j, g_j)
+        e[2 * j] = q[0 * N + j] / ell;
+        e[2 * j + 1] = q[1 * N + j] / ell;
+        e[2 * N + 2 * j] = q[2 * N + j] / l2;
+        e[2 * N + 2 * j + 1] = q[3 * N + j] / l2;
+        e[4 * N + 2 * j] = q[3 * N + j] / l2;
+        e[4 * N + 2 * j + 1] = q[4 * N + j] / l2;
+      }
+    }
+  });
+  if (err.st != HFD_OK) {
+    set_error("%s", err.msg);
+    return err.st;
+  }
+  P->degree_fallbacks = fallbacks.load();
+
+  // ---- flux edges and their stencils / weights
+  {
+    std::vector<uint8_t> need(E, 0);
+    for (int32_t e : P->div_eidx) need[e] = 1;
+    for (int64_t e = 0; e < E; ++e)
+      if (need[e]) P->flux_edges.push_back((int32_t)e);
+  }
+  const int64_t Ef = (int64_t)P->flux_edges.size();
+  P->stencil.assign(6 * Ef, 0);
+  P->normal.assign(2 * Ef, 0.0);
+  P->w5.assign(30 * Ef, 0.0);
+  P->w3.assign(18 * Ef, 0.0);
+  P->rank.assign(2 * Ef, 0);
+  static const int L3[3][3] = {{0, 1, 2}, {1, 2, 3}, {2, 3, 4}};
+  static const int R3[3][3] = {{5, 4, 3}, {4, 3, 2}, {3, 2, 1}};
+  parallel_for(Ef, nthreads, [&](int64_t f, int) {
+    int e = P->flux_edges[f];
+    int a = P->edges[2 * e], b = P->edges[2 * e + 1];
+    int used[6] = {a, b, 0, 0, 0, 0};
+    double dabx = P->dispx(a, b), daby = P->dispy(a, b);
+    double d1x, d1y, d2x, d2y, d3x, d3y, d4x, d4y;
+    int b1 = extend(*P, a, -dabx, -daby, used, 2, &d1x, &d1y);
+    if (b1 < 0) goto fail;
+    used[2] = b1;
+    {
+      int b2 = extend(*P, b1, d1x, d1y, used, 3, &d2x, &d2y);
+      if (b2 < 0) goto fail;
+      used[3] = b2;
+      int f1 = extend(*P, b, dabx, daby, used, 4, &d3x, &d3y);
+      if (f1 < 0) goto fail;
+      used[4] = f1;
+      int f2 = extend(*P, f1, d3x, d3y, used, 5, &d4x, &d4y);
+      if (f2 < 0) goto fail;
+      int ids[6] = {b2, b1, a, b, f1, f2};
+      double pos[6][2];
+      pos[2][0] = 0.0; pos[2][1] = 0.0;
+      pos[1][0] = d1x; pos[1][1] = d1y;
+      pos[0][0] = pos[1][0] + d2x; pos[0][1] = pos[1][1] + d2y;
+      pos[3][0] = dabx; pos[3][1] = daby;
+      pos[4][0] = pos[3][0] + d3x; pos[4][1] = pos[3][1] + d3y;
+      pos[5][0] = pos[4][0] + d4x; pos[5][1] = pos[4][1] + d4y;
+      double hx = 0.5 * pos[3][0], hy = 0.5 * pos[3][1];
+      double rel[6][2];
+      for (int k = 0; k < 6; ++k) { rel[k][0] = pos[k][0] - hx; rel[k][1] = pos[k][1] - hy; }
+      double ell = std::sqrt(dabx * dabx + daby * daby);
+      for (int k = 0; k < 6; ++k) P->stencil[6 * f + k] = ids[k];
+      P->normal[2 * f] = dabx / ell;
+      P->normal[2 * f + 1] = daby / ell;
+      int rl = five_node(&rel[0], ell, o->sv_rtol, &P->w5[30 * f]);
+      int rr = five_node(&rel[1], ell, o->sv_rtol, &P->w5[30 * f + 15]);
+      if (rl == 0 || rr == 0) {
+        err.set(HFD_ERR_SINGULAR, "5-node system kept no singular value");
+        return;
+      }
+      P->rank[2 * f] = rl;
+      P->rank[2 * f + 1] = rr;
+      for (int j = 0; j < 3; ++j) {
+        double r3[3][2];
+        int nearL = -1, nearR = -1;
+        for (int k = 0; k < 3; ++k) {
+          r3[k][0] = rel[L3[j][k]][0]; r3[k][1] = rel[L3[j][k]][1];
+          if (L3[j][k] == 2) nearL = k;
+        }
+        three_node(r3, nearL, &P->w3[18 * f + 3 * j]);
+        for (int k = 0; k < 3; ++k) {
+          r3[k][0] = rel[R3[j][k]][0]; r3[k][1] = rel[R3[j][k]][1];
+          if (R3[j][k] == 3) nearR = k;
+        }
+        three_node(r3, nearR, &P->w3[18 * f + 9 + 3 * j]);
+      }
+      return;
+    }
+  fail:
+    char m[160];
+    snprintf(m, sizeof m, "stencil of edge (%d,%d) cannot be extended (Sec. 2.1)", a, b);
+    err.set(HFD_ERR_STENCIL, m);
+  });
+  if (err.st != HFD_OK) {
+    set_error("%s", err.msg);
+    return err.st;
+  }
+  P->prep_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return HFD_OK;
+}
+
+}  // namespace hfd
+
+// ------------------------------------------------------------------ C ABI (host part)
+using hfd::Prep;
+
+extern "C" {
+
+void hfd_default_options(hfd_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->precision = 0;
+  o->div_degree = 5;
+  o->visc_degree = 4;
+  o->viscous = 0;
+  o->renumber = 1;
+  o->nthreads = 0;
+  o->gamma = 1.4;
+  o->mu = 0.0;
+  o->prandtl = 0.72;
+  o->R_gas = 1.0;
+  o->weno_eps = 1e-2;
+  o->sens_lo = 0.01;
+  o->sens_hi = 0.79;
+  o->sv_rtol = 1e-13;
+  o->div_cond_min = 1e-12;
+  o->harten = 0.1;
+  o->cfl = 0.3;
+}
+
+const char* hfd_last_error(void) { return hfd::last_error(); }
+
+hfd_status hfd_prep_create(const hfd_mesh_desc* desc, const hfd_options* opts, hfd_prep** out) {
+  if (!out) { hfd::set_error("hfd_prep_create: out is null"); return HFD_ERR_ARG; }
+  *out = nullptr;
+  hfd_options def;
+  if (!opts) { hfd_default_options(&def); opts = &def; }
+  hfd_prep* p = new (std::nothrow) hfd_prep();
+  if (!p) { hfd::set_error("hfd_prep_create: out of host memory"); return HFD_ERR_ARG; }
+  hfd_status st;
+  try {
+    st = hfd::build_prep(desc, opts, p);
+  } catch (const std::exception& e) {
+    hfd::set_error("hfd_prep_create: %s", e.what());
+    st = HFD_ERR_ARG;
+  }
+  if (st != HFD_OK) { delete p; return st; }
+  *out = p;
+  return HFD_OK;
+}
+
+void hfd_prep_destroy(hfd_prep* p) { delete p; }
+
+namespace {
+struct Arr { void* ptr; int64_t n; size_t elt; bool writable; };
+Arr lookup(const Prep* P, const char* name) {
+  auto I = [](const std::vector<int32_t>& v) {
+    return Arr{(void*)v.data(), (int64_t)v.size(), 4, false};
+  };
+  auto D = [](const std::vector<double>& v, bool w) {
+    return Arr{(void*)v.data(), (int64_t)v.size(), 8, w};
+  };
+  std::string s(name ? name : "");
+  if (s == "edges") return I(P->edges);
+  if (s == "flux_edges") return I(P->flux_edges);
+  if (s == "stencil") return I(P->stencil);
+  if (s == "normal") return D(P->normal, false);
+  if (s == "w5") return D(P->w5, true);
+  if (s == "w3") return D(P->w3, true);
+  if (s == "rank") return I(P->rank);
+  if (s == "active") return I(P->active);
+  if (s == "div_vptr") return I(P->div_vptr);
+  if (s == "div_vidx") return I(P->div_vidx);
+  if (s == "div_eptr") return I(P->div_eptr);
+  if (s == "div_eidx") return I(P->div_eidx);
+  if (s == "div_coef") return D(P->div_coef, true);
+  if (s == "div_degree") return I(P->div_degree);
+  if (s == "visc_coef") return D(P->visc_coef, true);
+  if (s == "lmin") return D(P->lmin, false);
+  return Arr{nullptr, -1, 0, false};
+}
+}  // namespace
+
+int64_t hfd_prep_size(const hfd_prep* p, const char* name) {
+  if (!p) return -1;
+  return lookup(p, name).n;
+}
+
+hfd_status hfd_prep_get(const hfd_prep* p, const char* name, void* dst, int64_t count) {
+  if (!p || !dst) { hfd::set_error("hfd_prep_get: null argument"); return HFD_ERR_ARG; }
+  Arr a = lookup(p, name);
+  if (a.n < 0 || count != a.n) {
+    hfd::set_error("hfd_prep_get: unknown array '%s' or wrong count", name ? name : "");
+    return HFD_ERR_ARG;
+  }
+  std::memcpy(dst, a.ptr, a.elt * (size_t)a.n);
+  return HFD_OK;
+}
+
+hfd_status hfd_prep_set(hfd_prep* p, const char* name, const void* src, int64_t count) {
+  if (!p || !src) { hfd::set_error("hfd_prep_set: null argument"); return HFD_ERR_ARG; }
+  Arr a = lookup(p, name);
+  if (a.n < 0 || count != a.n || !a.writable) {
+    hfd::set_error("hfd_prep_set: '%s' unknown, read-only or wrong count", name ? name : "");
+    return HFD_ERR_ARG;
+  }
+  std::memcpy(a.ptr, src, a.elt * (size_t)a.n);
+  return HFD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+"""CPU tests of the native library: it loads, exports every entry point of include/hfd.h, and
+its host preprocessing agrees with the oracle (no GPU is used)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_01286_gb300 as p
+    return p
+
+
+def test_library_exports_every_declared_entry_point(pkg):
+    hdr = open(os.path.join(ROOT, "include", "hfd.h")).read()
+    declared = set(re.findall(r"\b(hfd_[a-z_]+)\s*\(", hdr))
+    assert len(declared) >= 20
+    lib = pkg.hfd._lib
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared == set(pkg.hfd.EXPORTED)
+
+
+def test_default_options(pkg):
+    o = pkg.options()
+    assert (o.div_degree, o.visc_degree, o.precision, o.renumber) == (5, 4, 0, 1)
+    assert (o.sens_lo, o.sens_hi, o.weno_eps, o.cfl) == (0.01, 0.79, 1e-2, 0.3)
+
+
+@pytest.fixture(scope="module")
+def c1(pkg):
+    m = synth.jittered_grid(40, 40, 10.0, 10.0, seed=1)
+    return m, oracle.prepare(m), pkg.Prep(m)
+
+
+def test_host_prep_discrete_choices_match_oracle(c1):
+    m, P, prep = c1
+    np.testing.assert_array_equal(prep.get("edges").reshape(-1, 2), P.topo["edges"])
+    np.testing.assert_array_equal(prep.get("flux_edges"), P.edges)
+    np.testing.assert_array_equal(prep.get("stencil").reshape(-1, 6), P.stencil)
+    np.testing.assert_array_equal(prep.get("rank").reshape(-1, 2), P.rank)
+    np.testing.assert_array_equal(prep.get("active"), P.active)
+    np.testing.assert_array_equal(prep.get("div_degree"), P.div_degree)
+
+
+def test_host_prep_coefficients_match_oracle(c1):
+    m, P, prep = c1
+    from gpu_helpers import oracle_blocks
+    # 3-node weights: both sides round the exact (rational) weights -> equal
+    np.testing.assert_allclose(prep.get("w3").reshape(-1, 2, 3, 3), P.w3, rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(prep.get("normal").reshape(-1, 2), P.normal)
+    # divergence rows: full-rank least squares, condition ~1e3
+    ref = oracle_blocks(P, len(m["x"]))["div_coef"]
+    got = prep.get("div_coef")
+    assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
+    # 5-node weights: truncated pseudo-inverses; most agree to ~1e-13, the ill-conditioned few
+    # (small retained singular values) to ~1e-7
+    d = np.abs(prep.get("w5").reshape(-1, 2, 15) - P.w5).max(axis=(1, 2))
+    assert np.median(d) < 1e-12
+    assert np.mean(d < 1e-10) > 0.95
+    assert d.max() < 1e-6
+
+
+def test_host_prep_viscous_rows_match_oracle(pkg):
+    m = synth.jittered_grid(16, 16, 2 * np.pi, 2 * np.pi, seed=3)
+    P = oracle.prepare(m, oracle.Options(viscous=True, mu=0.01))
+    prep = pkg.Prep(m, viscous=True, mu=0.01)
+    from gpu_helpers import oracle_blocks
+    ref = oracle_blocks(P, len(m["x"]))["visc_coef"]
+    got = prep.get("visc_coef")
+    assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_host_prep_with_ghosts_matches_oracle(pkg):
+    m = synth.jittered_box_with_ghosts(20, 16, (0.0, 1.0), (0.0, 1.0), 5, seed=2)
+    P = oracle.prepare(m)
+    prep = pkg.Prep(m)
+    np.testing.assert_array_equal(prep.get("flux_edges"), P.edges)
+    np.testing.assert_array_equal(prep.get("stencil").reshape(-1, 6), P.stencil)
+    np.testing.assert_array_equal(prep.get("active"), P.active)
+
+
+def test_invalid_meshes_are_rejected(pkg):
+    m = synth.jittered_grid(6, 6, 1.0, 1.0, seed=0)
+    bad = dict(m)
+    bad["tri"] = m["tri"].copy()
+    bad["tri"][0, 0] = 10 ** 6
+    with pytest.raises(pkg.HfdError) as e:
+        pkg.Prep(bad)
+    assert e.value.status == 2
+    bad = dict(m)
+    bad["tri"] = np.concatenate([m["tri"], m["tri"][:1]])      # edge in three triangles
+    with pytest.raises(pkg.HfdError) as e:
+        pkg.Prep(bad)
+    assert e.value.status == 2
+    with pytest.raises(pkg.HfdError) as e:
+        pkg.Prep(m, div_degree=9)
+    assert e.value.status == 1
+    # two triangles: no edge has enough neighbours for a 6-node stencil
+    tiny = {"x": np.array([0.0, 1.0, 1.0, 0.0]), "y": np.array([0.0, 0.0, 1.0, 1.0]),
+            "tri": np.array([[0, 1, 2], [0, 2, 3]]), "periodic_x": False, "periodic_y": False}
+    with pytest.raises(pkg.HfdError) as e:
+        pkg.Prep(tiny)
+    assert e.value.status == 3
