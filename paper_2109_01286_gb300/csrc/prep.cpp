@@ -230,6 +230,25 @@ static double ls_rows(int m, int n, std::vector<double>& A, const int (*targets)
   return rnn / r11;
 }
 
+// Minimum-norm rows e_t^T A^+ of a possibly rank-deficient A (m x n, column-major) by the
+// one-sided Jacobi SVD of A (singular values <= max(m, n) * eps * sigma_max count as zero, the
+// convention of numpy's pinv): A^+ = V diag(1/s) U^T with U diag(s) = A V.
+static void pinv_rows_svd(int m, int n, const std::vector<double>& A, const int* targets,
+                          int ntarg, double* rows /* ntarg x m */) {
+  std::vector<double> W(A), V((size_t)n * n), s(n);
+  jacobi_svd(m, n, W.data(), V.data(), s.data());
+  double tol = std::max(m, n) * 2.220446049250313e-16 * s[0];
+  for (int t = 0; t < ntarg; ++t) {
+    double* r = rows + (size_t)t * m;
+    for (int i = 0; i < m; ++i) r[i] = 0.0;
+    for (int k = 0; k < n; ++k) {
+      if (!(s[k] > tol)) break;
+      double f = V[targets[t] + (size_t)k * n] / (s[k] * s[k]);   // V[t,k] U[:,k] / s_k
+      for (int i = 0; i < m; ++i) r[i] += f * W[i + (size_t)k * m];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ double-double (Dekker)
 struct dd { double hi, lo; };
 static inline dd two_sum(double a, double b) {
@@ -629,13 +648,14 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
         taylor(xv[2 * j], xv[2 * j + 1], o->visc_degree, p, nullptr, nullptr);
         for (int k = 0; k < K; ++k) B[j + (size_t)k * N] = p[k];
       }
-      if (N < K) {
-        err.set(HFD_ERR_SINGULAR, "viscous stencil has fewer vertices than basis terms");
-        return;
-      }
       const int targ[5][2] = {{1, -1}, {2, -1}, {3, -1}, {4, -1}, {5, -1}};
       std::vector<double> q(5 * (size_t)N);
-      ls_rows(N, K, B, targ, 5, q.data());
+      if (N >= K) {
+        ls_rows(N, K, B, targ, 5, q.data());
+      } else {            // fewer stencil vertices than basis terms: minimum-norm solution
+        const int t1[5] = {1, 2, 3, 4, 5};
+        pinv_rows_svd(N, K, B, t1, 5, q.data());
+      }
       double* e = &P->visc_coef[P->visc_cptr[r]];
       double l2 = ell * ell;
       for (int j = 0; j < N; ++j) {           // rows over interleaved (f_j, g_j)

@@ -70,8 +70,9 @@ def test_host_prep_coefficients_match_oracle(c1):
     assert d.max() < 1e-6
 
 
-def test_host_prep_viscous_rows_match_oracle(pkg):
-    m = synth.jittered_grid(16, 16, 2 * np.pi, 2 * np.pi, seed=3)
+@pytest.mark.parametrize("n", [16, 24])
+def test_host_prep_viscous_rows_match_oracle(pkg, n):
+    m = synth.jittered_grid(n, n, 2 * np.pi, 2 * np.pi, seed=3)
     P = oracle.prepare(m, oracle.Options(viscous=True, mu=0.01))
     prep = pkg.Prep(m, viscous=True, mu=0.01)
     from gpu_helpers import oracle_blocks
