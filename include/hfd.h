@@ -181,6 +181,22 @@ hfd_status hfd_steps_host(hfd_mesh* mesh, const double* U_in, double* U_out, dou
 hfd_status hfd_steps_profiled(hfd_mesh* mesh, double* U, double dt, int32_t nsteps, void* stream,
                               double* kernel_ms, int64_t* launches);
 
+/* hfd_residual without device allocation.  The paper has no counterpart: this entry point is
+ * for callers that cannot allocate device memory when they evaluate residuals -- applications
+ * that reserve all device memory for their own pool up front, and code that must not call
+ * cudaMalloc/cudaFree (which can synchronise the device) while other work runs.  Same inputs,
+ * output and result as hfd_residual (U in/out for its ghost columns, R out, both 12*nv device
+ * arrays in internal order), but the per-call scratch (state copy, vertex and edge fluxes) is a
+ * fixed 8 MiB array compiled into the library, held on every GPU that loads the library until
+ * the process exits.  That is room for about 32,000 vertices in FP64 (256 bytes each with their
+ * ~3 flux edges) or 65,000 in FP32 bulk; larger meshes get HFD_ERR_ARG with the bytes needed.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current), so make that first call before any stream capture.  All calls on a
+ * device share the array: calls that overlap on the GPU race and must be serialised by the
+ * caller.  Every call rewrites what it reads, so nothing carries over between calls.  Errors:
+ * HFD_ERR_ARG (sizes, null pointers, mesh not on the current device), HFD_ERR_CUDA. */
+hfd_status hfd_residual_static(hfd_mesh* mesh, double* U, double* R, void* stream);
+
 /* dt used by the most recent step (synchronises the stream). */
 hfd_status hfd_last_dt(hfd_mesh* mesh, double* dt, void* stream);
 

@@ -11,33 +11,12 @@
 #include <vector>
 
 #include "kernels.hpp"
+#include "mesh.hpp"
 #include "prep.hpp"
 
 using hfd::DevMesh;
 using hfd::Phys;
 using hfd::set_error;
-
-struct GraphEntry {
-  cudaGraphExec_t exec = nullptr;
-};
-
-struct hfd_mesh {
-  hfd_options opts{};
-  DevMesh dm;
-  Phys ph{};
-  int lanes = 8;
-  std::vector<int32_t> perm;            // internal -> input
-  int32_t* dperm = nullptr;             // device copy of perm
-  double* U1 = nullptr;                 // stage buffers 12 x V
-  double* U2 = nullptr;
-  double* Uin = nullptr;                // end-to-end staging (input order)
-  double* Uint = nullptr;               // end-to-end staging (internal order)
-  cudaStream_t cap = nullptr;           // private stream used for graph capture
-  std::map<std::pair<const double*, double>, GraphEntry> graphs;
-  hfd_mesh_stats stats{};
-  std::vector<void*> allocs;
-  int device = 0;
-};
 
 #define CK(call)                                                                   \
   do {                                                                             \

@@ -26,7 +26,7 @@ EXPORTED = ["hfd_default_options", "hfd_last_error", "hfd_prep_create", "hfd_pre
             "hfd_prep_size", "hfd_prep_get", "hfd_prep_set", "hfd_mesh_create", "hfd_mesh_upload",
             "hfd_mesh_destroy", "hfd_mesh_info", "hfd_mesh_perm", "hfd_state_import",
             "hfd_state_export", "hfd_residual", "hfd_step", "hfd_steps", "hfd_steps_host",
-            "hfd_last_dt", "hfd_check", "hfd_steps_profiled"]
+            "hfd_last_dt", "hfd_check", "hfd_steps_profiled", "hfd_residual_static"]
 
 
 class HfdError(RuntimeError):
@@ -86,6 +86,7 @@ _lib.hfd_mesh_perm.argtypes = [_P, _P]
 _lib.hfd_state_import.argtypes = [_P, _P, _P, _P]
 _lib.hfd_state_export.argtypes = [_P, _P, _P, _P]
 _lib.hfd_residual.argtypes = [_P, _P, _P, _P]
+_lib.hfd_residual_static.argtypes = [_P, _P, _P, _P]
 _lib.hfd_step.argtypes = [_P, _P, ctypes.c_double, _P]
 _lib.hfd_steps.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int32, _P]
 _lib.hfd_steps_host.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_int32, _P]
@@ -242,6 +243,13 @@ class Mesh:
         import torch
         R = torch.empty_like(U) if R is None else R
         _ok(_lib.hfd_residual(self._h, _dptr(U), _dptr(R), _stream(stream)), "hfd_residual")
+        return R
+
+    def residual_static(self, U, R, stream=None):
+        """hfd_residual_static: the residual with the library's fixed scratch array, for callers
+        that cannot allocate device memory at call time (R must be preallocated)."""
+        _ok(_lib.hfd_residual_static(self._h, _dptr(U), _dptr(R), _stream(stream)),
+            "hfd_residual_static")
         return R
 
     def step(self, U, dt=0.0, stream=None):
