@@ -488,8 +488,9 @@ def roe_flux(wl, wr, nx, ny, gamma, harten=0.1):
     qn = u * nx + v * ny
     lam = np.stack([qn - c, qn, qn, qn + c], -1)
     delta = harten * c
-    a = np.abs(lam)
-    a = np.where(a < delta[..., None], (lam * lam + delta[..., None] ** 2) / (2.0 * delta[..., None]), a)
+    a = np.where(np.real(lam) < 0, -lam, lam)          # |lambda| (real-part sign: complex-step safe)
+    a = np.where(np.real(a) < np.real(delta[..., None]),
+                 (lam * lam + delta[..., None] ** 2) / (2.0 * delta[..., None]), a)
     dw = np.moveaxis(wr - wl, 0, -1)
     alpha = np.einsum("...ij,...j->...i", L, dw)
     diss = np.einsum("...ij,...j->...i", R, a * alpha)
@@ -517,9 +518,13 @@ def edge_values(P, U, opts, diag=None):
     """Left/right midpoint states of every needed edge by Alg. 1 (Sec. 2.3) with the branch
     sense of Eq. (2d_hweno_intp) (R1: 5-node value when sens_lo < omega_1 < sens_hi, else the
     omega-weighted 3-node values), per characteristic component and side; then R16 positivity."""
+    return edge_values_from_stencil(P, U[:, P.stencil], opts, diag)
+
+
+def edge_values_from_stencil(P, W, opts, diag=None):
+    """edge_values on the gathered stencil states W (12, Ee, 6); works on complex input
+    (branch and positivity decisions use real parts) for complex-step derivatives."""
     g = opts.gamma
-    S = P.stencil
-    W = U[:, S]                                   # (12, Ee, 6)
     wi, wj = W[0:4, :, 2], W[0:4, :, 3]
     u, v, H, c = roe_average(wi, wj, g)
     L, R = eigenvectors(u, v, H, c, P.normal[:, 0], P.normal[:, 1], g)
@@ -535,7 +540,7 @@ def edge_values(P, U, opts, diag=None):
         o1, o2, o3 = weno_weights(*[C[0][:, :, k] for k in order], opts.weno_eps)
         c3 = [np.einsum("en,eqn->eq", P.w3[:, side, j], C[0][:, :, three[j]]) for j in range(3)]
         weighted = o1 * c3[0] + o2 * c3[1] + o3 * c3[2]
-        smooth = (o1 > opts.sens_lo) & (o1 < opts.sens_hi)
+        smooth = (np.real(o1) > opts.sens_lo) & (np.real(o1) < opts.sens_hi)
         cs = np.where(smooth, c5, weighted)
         ws = np.einsum("eij,ej->ie", R, cs)          # back-projection w = R c
         if diag is not None:
@@ -543,13 +548,19 @@ def edge_values(P, U, opts, diag=None):
             diag.setdefault("smooth", []).append(smooth)
         out.append(ws)
     wl, wr = out
-    bad_l = (wl[0] <= 0) | (pressure(wl, g) <= 0)
-    bad_r = (wr[0] <= 0) | (pressure(wr, g) <= 0)
+    bad_l = (np.real(wl[0]) <= 0) | (np.real(pressure(wl, g)) <= 0)
+    bad_r = (np.real(wr[0]) <= 0) | (np.real(pressure(wr, g)) <= 0)
     wl = np.where(bad_l[None], wi, wl)
     wr = np.where(bad_r[None], wj, wr)
     if diag is not None:
         diag["positivity_fallbacks"] = int(bad_l.sum() + bad_r.sum())
     return wl, wr
+
+
+def edge_flux_from_stencil(P, W, opts):
+    """Numerical flux h (4, Ee) of every needed edge from its gathered stencil states."""
+    wl, wr = edge_values_from_stencil(P, W, opts)
+    return roe_flux(wl, wr, P.normal[:, 0], P.normal[:, 1], opts.gamma, opts.harten)
 
 
 def residual(mesh, P, U, opts=None, diag=None):
@@ -564,9 +575,9 @@ def residual(mesh, P, U, opts=None, diag=None):
     wl, wr = edge_values(P, U, opts, diag)
     h = roe_flux(wl, wr, P.normal[:, 0], P.normal[:, 1], g, opts.harten)   # (4, Ee)
     E = len(P.topo["edges"])
-    Rm = np.zeros((12, V))
+    Rm = np.zeros((12, V), dtype=U.dtype)
     for q in range(4):
-        z = np.zeros(2 * V + E)
+        z = np.zeros(2 * V + E, dtype=U.dtype)
         z[0:2 * V:2] = F[q]
         z[1:2 * V:2] = G[q]
         z[2 * V + P.edges] = h[q]
@@ -575,7 +586,7 @@ def residual(mesh, P, U, opts=None, diag=None):
     if opts.viscous:
         Fv, Gv = viscous_flux(U, opts)
         for q in range(4):
-            z = np.zeros(2 * V)
+            z = np.zeros(2 * V, dtype=U.dtype)
             z[0::2] = Fv[q]
             z[1::2] = Gv[q]
             for k in range(3):

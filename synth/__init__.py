@@ -9,7 +9,8 @@ problem, planar Sod, Taylor-Green vortex).
 from .meshes import jittered_grid, jittered_box_with_ghosts, mesh_summary
 from .states import (GAMMA, isentropic_vortex, four_quadrant, planar_sod, taylor_green,
                      uniform_state, prim_to_cons)
+from .workloads import batched_vortices
 
 __all__ = ["jittered_grid", "jittered_box_with_ghosts", "mesh_summary", "GAMMA",
            "isentropic_vortex", "four_quadrant", "planar_sod", "taylor_green",
-           "uniform_state", "prim_to_cons"]
+           "uniform_state", "prim_to_cons", "batched_vortices"]

@@ -537,3 +537,39 @@ def test_linearised_residual_has_growing_modes():
         J[:, k] = (oracle.residual(m, P, U.reshape(12, -1)) - R0).ravel() / eps
     growth = np.linalg.eigvals(J).real.max() / n
     assert growth > 0.05
+
+
+@pytest.mark.parametrize("kind", ["periodic", "ghosts", "viscous"])
+def test_oracle_adjoint_dot_product_against_complex_step(kind):
+    """<lam, J delta> with J delta by the complex-step method through the whole oracle (exact to
+    rounding) must equal <J^T lam, delta> from the hand-assembled adjoint, for the residual and
+    for one SSP-RK3 step.  Pins the adjoint (and the transposed divergence rows, vertex-flux and
+    edge-flux Jacobians, ghost transpose and RK3 reversal) against the forward oracle."""
+    from oracle import adjoint as ADJ
+    rng = np.random.default_rng(1)
+    opts = oracle.Options()
+    if kind == "periodic":
+        m = synth.jittered_grid(10, 10, 4.0, 4.0, seed=3)
+        U = synth.isentropic_vortex(m, center=(2.0, 2.0), beta=3.0)
+    elif kind == "ghosts":
+        m = synth.jittered_box_with_ghosts(10, 10, (0.0, 1.0), (0.0, 1.0), 5, seed=2)
+        U = synth.uniform_state(m)
+        U[:4] *= 1.0 + 0.05 * np.sin(3.0 * m["x"])[None]
+        U[4:] = 0.01 * rng.standard_normal((8, U.shape[1]))
+    else:
+        m = synth.jittered_grid(10, 10, 2 * np.pi, 2 * np.pi, seed=3)
+        opts = oracle.Options(viscous=True, mu=0.05, R_gas=1.0 / (1.4 * 0.01))
+        U = synth.taylor_green(m)
+    P = oracle.prepare(m, opts)
+    V = U.shape[1]
+    mu, delta = rng.standard_normal((12, V)), rng.standard_normal((12, V))
+    Uc = U.astype(complex) + 1e-30j * delta
+    Rj = oracle.residual(m, P, Uc.copy(), opts).imag / 1e-30
+    lhs = np.sum(mu[:, P.active] * Rj[:, P.active])
+    rhs = np.sum(ADJ.residual_vjp(m, P, U, mu, opts) * delta)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    dt = 0.5 * oracle.cfl_dt(m, P, U)
+    Sj = oracle.step(m, P, Uc.copy(), dt, opts).imag / 1e-30
+    lhs = np.sum(mu * Sj)
+    rhs = np.sum(ADJ.step_vjp(m, P, U, dt, mu, opts) * delta)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
