@@ -34,7 +34,7 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "vertex-stage updates/s"
-FP64_NOMINAL_FLOPS = 1.25e12     # GB300 FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x ~2.07 GHz
+FP64_PEAK_FLOPS = 1.258e12       # GB300 FP64: 152 SMs x 2 DFMA/clk (ncu peak_sustained) x 2 x 2.07 GHz
 CPU_PATCH_N = 32                 # bounded oracle sample: 32 x 32 patch of the same workload
 
 
@@ -47,6 +47,12 @@ def parse():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="four-quadrant",
+                    choices=["four-quadrant", "batched", "adjoint", "tgv"],
+                    help="batched: 256 uneven isentropic-vortex meshes advanced together; "
+                         "adjoint: gradient of a 200-step vortex run, checked by differences")
+    ap.add_argument("--directions", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=256)
     return ap.parse_args()
 
 
@@ -114,7 +120,9 @@ def algorithmic_costs(stats, T):
     the mesh's actual sizes.  T = bytes of the bulk type.  Per-unit figures:
       vertex : 96 B state read + 12T AoS copy + 8T fluxes written, ~30 flop  per vertex
       edge   : 24 B stencil + 2T normal + 48T weights + 4T flux written     per flux edge,
-               + 12T state copy read once per vertex; ~1530 flop per edge (smooth branch)
+               + 12T state copy read once per vertex; 480 bulk-precision flop per edge on the
+               smooth branch (5-node sums in conservative variables 240, Roe flux ~200, end-state
+               differences 24, positivity 12; a division or square root counts as one flop)
       div    : 8 B row pointers + (4 B + 6T) per stencil vertex + (4 B + 3T) per stencil edge
                + 96 B stage state + 96 B base state (2 of 3 stages) + 96 B written per vertex,
                + 8T fluxes per vertex and 4T per edge read once; 48 flop per stencil vertex,
@@ -123,7 +131,7 @@ def algorithmic_costs(stats, T):
     nv, ne = stats["div_nv_total"], stats["div_ne_total"]
     return {
         "vertex": {"bytes": V * (96 + 20 * T), "flops": 30 * V},
-        "edge": {"bytes": Ef * (24 + 54 * T) + V * 12 * T, "flops": 1530 * Ef},
+        "edge": {"bytes": Ef * (24 + 54 * T) + V * 12 * T, "flops": 480 * Ef},
         "div": {"bytes": A * (8 + 96 * (1 + 2.0 / 3.0) + 96) + nv * (4 + 6 * T) + ne * (4 + 3 * T)
                 + V * 8 * T + Ef * 4 * T, "flops": 48 * nv + 24 * ne + 48 * A},
         "ghost": {"bytes": (V - A) * (12 + 96 + 96), "flops": 0},
@@ -226,17 +234,24 @@ def run_native(args):
         dm = prep.upload(prec)
         st = dm.stats_dict()
         Ui = dm.import_state(U_dev)
-        W = Ui.clone()
-        dm.steps(W, 0.0, args.warmup)
+        # Every timed step advances the initial state of the workload: the method as read here
+        # is unstable on this problem and its state turns non-finite within a few steps, after
+        # which the sensor takes its re-decision path everywhere.  The device copy that resets
+        # the state is inside the timed region.
+        X = torch.empty_like(Ui)
+        for _ in range(args.warmup):
+            X.copy_(Ui)
+            dm.steps(X, 0.0, 1)
         torch.cuda.synchronize()
-        X = Ui.clone()
         barrier()
         clk = Clocks(local) if prec == "fp64" else None
         if clk:
             clk.start()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        dm.steps(X, 0.0, args.steps)
+        for _ in range(args.steps):
+            X.copy_(Ui)
+            dm.steps(X, 0.0, 1)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -251,8 +266,14 @@ def run_native(args):
         A = st["nactive"]
         value = world * A * 3 * args.steps / (ms / 1000.0)
         # second pass: the same steps launched kernel by kernel with events
-        Y = Ui.clone()
-        kms, nl = dm.steps_profiled(Y, 0.0, args.steps)
+        kms = {k: 0.0 for k in ("ghost", "vertex", "edge", "div", "dt")}
+        nl = 0
+        for _ in range(args.steps):
+            X.copy_(Ui)
+            km, n = dm.steps_profiled(X, 0.0, 1)
+            nl += n
+            for k in kms:
+                kms[k] += km[k]
         T = 8 if prec == "fp64" else 4
         costs = algorithmic_costs(st, T)
         launches_per_kind = {"vertex": 3 * args.steps, "edge": 3 * args.steps,
@@ -297,9 +318,10 @@ def run_native(args):
     dom = max(r["kernels"], key=lambda k: r["kernels"][k]["share"])
     kd = r["kernels"][dom]
     roof = {"kernel": f"k_{dom}<double>", "bound": "alu", "achieved": kd["tflops"],
-            "peak": FP64_NOMINAL_FLOPS / 1e12, "unit": "TFLOP/s",
-            "frac": kd["tflops"] / (FP64_NOMINAL_FLOPS / 1e12), "traffic": None,
-            "peak_source": "nominal GB300 FP64 (MEASURED_PEAKS.json has no FP64 figure)",
+            "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+            "frac": kd["tflops"] / (FP64_PEAK_FLOPS / 1e12), "traffic": None,
+            "peak_source": "derived: ncu dfma peak_sustained 2/SM/clk x 152 SMs x 2 flop x 2.07 GHz "
+                           "(MEASURED_PEAKS.json has no FP64 figure)",
             "hbm_gbs": kd["gbs"], "hbm_frac": kd["gbs"] / peak_hbm,
             "hbm_peak_source": peak_src}
     f32 = results["fp32"]
@@ -311,6 +333,8 @@ def run_native(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": workload_name(args.n), "precision": "fp64",
+                   "step_input": "every timed step advances the initial state (device reset "
+                                 "copy inside the timed region)",
                    "physical_vertices": r["stats"]["nactive"], "stored_vertices": r["stats"]["nv"],
                    "flux_edges": r["stats"]["nflux_edges"], "time_step": "device CFL 0.3",
                    "l2": "no flush: per-stage working set (state, coefficients) is several GB, "
@@ -339,10 +363,244 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batched workload
+def run_batched(args):
+    """Many uneven meshes advanced together (one union mesh, autotuned launch shape, graph of RK
+    stages) against looping the same meshes one at a time (one graph per mesh)."""
+    import torch
+    from paper_2109_01286_gb300 import Prep
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    members = synth.batched_vortices(n=args.batch, seed=4)
+    t0 = time.perf_counter()
+    preps = [Prep(x["mesh"]) for x in members]
+    prep_s = time.perf_counter() - t0
+    Ub = np.concatenate([x["U"] for x in members], axis=1)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for prec in ("fp64", "fp32"):
+        batch = Prep.concat(preps).upload(prec)
+        A = batch.stats.nactive
+        U0 = batch.import_state(torch.from_numpy(Ub).cuda())
+        choice = batch.autotune(U0)
+        W = U0.clone()
+        batch.steps(W, 0.0, args.warmup)
+        X = U0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.steps(X, 0.0, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms, nl = batch.steps_profiled(U0.clone(), 0.0, args.steps)
+        del batch, W, X
+        torch.cuda.empty_cache()
+        # the same meshes one at a time
+        singles = [p.upload(prec) for p in preps]
+        states = [s.import_state(torch.from_numpy(x["U"]).cuda()) for s, x in zip(singles, members)]
+        for s, u in zip(singles, states):
+            s.steps(u.clone(), 0.0, args.warmup)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s, u in zip(singles, states):
+            s.steps(u, 0.0, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_loop = e0.elapsed_time(e1)
+        del singles, states
+        torch.cuda.empty_cache()
+        out[prec] = {"value": A * 3 * args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps,
+                     "looped_singles_value": A * 3 * args.steps / (ms_loop / 1000.0),
+                     "looped_singles_ms_per_step": ms_loop / args.steps,
+                     "speedup_vs_looped": ms_loop / ms,
+                     "launch": {"persistent": choice[0], "grid": choice[1]},
+                     "kernels_ms": kms, "launches": nl}
+    r = out["fp64"]
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": "vertex-stage/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "workload": "batched",
+        "config": {"workload": f"{args.batch} isentropic vortices, vertex counts log-uniform in "
+                               "[2e3, 6.4e4], aspect 1-4, jittered random-split periodic meshes",
+                   "physical_vertices": int(sum(x["U"].shape[1] for x in members)),
+                   "prep_seconds": prep_s, "time_step": "device CFL 0.3 per member"},
+        "fp64": out["fp64"], "fp32_bulk": out["fp32"], "gpu_launches": int(r["launches"]),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ adjoint workload
+def run_adjoint(args):
+    """Discrete adjoint of a 200-step isentropic-vortex run on a 256 x 256 jittered mesh (FP64,
+    checkpoint every 20 steps): objective J = sum_v A_v (rho - rho_exact)^2 at the final time;
+    gradients with respect to the initial state (and its derivatives) and to the vortex strength
+    beta, checked against central differences (step 1e-6) on random directions.  Reports the
+    cost of the backward pass relative to the forward pass."""
+    import torch
+    import oracle
+    from paper_2109_01286_gb300 import Mesh
+    from paper_2109_01286_gb300.autograd import rollout
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n, nsteps, every, beta = 256, 200, 20, 5.0
+    m = synth.jittered_grid(n, n, 10.0, 10.0, seed=5)
+    mesh = Mesh(m)
+    U0 = synth.isentropic_vortex(m, beta=beta)
+    # fixed step: the device CFL step (CFL 0.3) of the initial state
+    probe = mesh.import_state(torch.from_numpy(U0).cuda())
+    mesh.step(probe, 0.0)
+    dt = float(mesh.last_dt())
+    del probe
+    T = nsteps * dt
+    perm = torch.from_numpy(mesh.perm.astype(np.int64)).cuda()
+    area = torch.from_numpy(oracle.vertex_areas(m)).cuda()[perm]
+    rho_ex = torch.from_numpy(synth.isentropic_vortex(m, beta=beta, t=T)[0]).cuda()[perm]
+
+    def J(Ui):
+        UN = rollout(Ui, mesh, dt, nsteps, every)
+        return torch.sum(area * (UN[0] - rho_ex) ** 2)
+
+    U0i = mesh.import_state(torch.from_numpy(U0).cuda()).requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    val = J(U0i)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    val.backward()
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    g = U0i.grad.detach()
+    # per-step cost: forward step against one adjoint step (same state)
+    X = U0i.detach().clone()
+    lam = torch.randn_like(X)
+    out = torch.empty_like(X)
+    for _ in range(3):
+        mesh.step(X.clone(), dt)
+        mesh.adjoint(X, lam, out, dt)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        mesh.step(X, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / 20
+    e0.record()
+    for _ in range(20):
+        mesh.adjoint(X, lam, out, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_adj = e0.elapsed_time(e1) / 20
+    # central differences on random directions of the initial state
+    rng = np.random.default_rng(5)
+    rel = []
+    with torch.no_grad():
+        for _ in range(args.directions):
+            d = mesh.import_state(torch.from_numpy(rng.standard_normal(U0.shape)).cuda())
+            d = d / torch.linalg.norm(d)
+            eps = 1e-6
+            fd = (J(U0i.detach() + eps * d).item() - J(U0i.detach() - eps * d).item()) / (2 * eps)
+            ad = torch.sum(g * d).item()
+            rel.append(abs(fd - ad) / max(abs(fd), abs(ad), 1e-300))
+    # vortex strength: dJ/dbeta = <g, dU0/dbeta> - 2 sum A (rho - rho_ex) drho_ex/dbeta, with the
+    # beta derivatives of the (synthetic) exact states by 4th-order central differences
+    db = 1e-3
+    def ic(bb, t=0.0):
+        return synth.isentropic_vortex(m, beta=bb, t=t)
+    dU0 = (-ic(beta + 2 * db) + 8 * ic(beta + db) - 8 * ic(beta - db) + ic(beta - 2 * db)) / (12 * db)
+    drho = (-ic(beta + 2 * db, T)[0] + 8 * ic(beta + db, T)[0] - 8 * ic(beta - db, T)[0]
+            + ic(beta - 2 * db, T)[0]) / (12 * db)
+    with torch.no_grad():
+        UN = rollout(U0i.detach(), mesh, dt, nsteps, every)
+        resid = UN[0] - rho_ex
+    dJdb = torch.sum(g * mesh.import_state(torch.from_numpy(dU0).cuda())).item() \
+        - 2.0 * torch.sum(area * resid * torch.from_numpy(drho).cuda()[perm]).item()
+    with torch.no_grad():
+        def Jb(bb):
+            Ub = mesh.import_state(torch.from_numpy(ic(bb)).cuda())
+            re = torch.from_numpy(ic(bb, T)[0]).cuda()[perm]
+            return torch.sum(area * (rollout(Ub, mesh, dt, nsteps, every)[0] - re) ** 2).item()
+        fd_b = (Jb(beta + 1e-6) - Jb(beta - 1e-6)) / 2e-6
+    line = {
+        "metric": "adjoint check and cost", "workload": "adjoint",
+        "config": {"workload": f"isentropic vortex beta={beta}, {n}x{n} jittered random-split "
+                               f"periodic mesh, FP64, {nsteps} SSP-RK3 steps, dt={dt:.5g}, "
+                               f"checkpoint every {every}",
+                   "objective": "sum_v A_v (rho - rho_exact)^2 at t_final"},
+        "J": val.item(), "t_final": T,
+        "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
+        "ms_step": ms_step, "ms_adjoint_step": ms_adj, "adjoint_over_step": ms_adj / ms_step,
+        "fd_directions": args.directions, "fd_rel_err_max": max(rel),
+        "fd_rel_err_median": float(np.median(rel)),
+        "dJ_dbeta_adjoint": dJdb, "dJ_dbeta_fd": fd_b,
+        "dJ_dbeta_rel_err": abs(dJdb - fd_b) / abs(fd_b),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ viscous accuracy workload
+def run_tgv(args):
+    """Decaying Taylor-Green vortex (Re 100, Mach 0.1, Pr 0.72) on a 512 x 512 jittered
+    periodic mesh to t = 1, FP64 and FP32 bulk: relative L2 difference of the two paths and the
+    velocity error of each against the incompressible decay exp(-2 nu t)."""
+    import torch
+    from paper_2109_01286_gb300 import Prep
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n, mach, re, tend = args.n if args.n != 1024 else 512, 0.1, 100.0, 1.0
+    p0 = 1.0 / (1.4 * mach * mach)
+    m = synth.jittered_grid(n, n, 2 * np.pi, 2 * np.pi, seed=3)
+    U0 = synth.taylor_green(m, mach=mach)
+    prep = Prep(m, viscous=True, mu=1.0 / re, R_gas=p0, prandtl=0.72)
+    h = 2 * np.pi / n
+    dt = 0.3 * h / (1.0 + np.sqrt(1.4 * p0))
+    nsteps = int(np.ceil(tend / dt))
+    dt = tend / nsteps
+    out = {}
+    for prec in ("fp64", "fp32"):
+        mesh = prep.upload(prec)
+        X = mesh.import_state(torch.from_numpy(U0).cuda())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mesh.steps(X, dt, nsteps)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        fin = True
+        try:
+            mesh.check()
+        except Exception:
+            fin = False
+        out[prec] = (mesh.export_state(X).cpu().numpy(), wall, fin)
+    a, b = out["fp64"][0], out["fp32"][0]
+    decay = np.exp(-2.0 * (1.0 / re) * tend)
+    uex = np.sin(m["x"]) * np.cos(m["y"]) * decay
+    vex = -np.cos(m["x"]) * np.sin(m["y"]) * decay
+
+    def vel_err(U):
+        u, v = U[1] / U[0], U[2] / U[0]
+        return float(np.sqrt(np.mean((u - uex) ** 2 + (v - vex) ** 2) / np.mean(uex ** 2 + vex ** 2)))
+    line = {
+        "metric": "mixed-precision accuracy", "workload": "tgv",
+        "config": {"workload": f"Taylor-Green vortex Re {re:g}, Mach {mach}, Pr 0.72, {n}x{n} "
+                               f"jittered periodic mesh, t = {tend}, {nsteps} steps of {dt:.4g}"},
+        "fp32_vs_fp64_rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(a)),
+        "fp32_vs_fp64_rel_l2_w": float(np.linalg.norm(a[:4] - b[:4]) / np.linalg.norm(a[:4])),
+        "velocity_rel_l2_vs_exp_decay": {"fp64": vel_err(a), "fp32": vel_err(b)},
+        "finite": {"fp64": out["fp64"][2], "fp32": out["fp32"][2]},
+        "wall_s": {"fp64": out["fp64"][1], "fp32": out["fp32"][1]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
+    elif args.workload == "tgv":
+        run_tgv(args)
     else:
         run_native(args)
 

@@ -97,6 +97,7 @@ typedef struct {
   int64_t div_degree_fallbacks;
   int64_t device_bytes;    /* device memory held by the mesh                                */
   double prep_seconds;     /* host preprocessing wall time                                  */
+  int32_t nmember;         /* meshes in a batch (hfd_prep_concat), 1 otherwise              */
 } hfd_mesh_stats;
 
 typedef struct hfd_prep hfd_prep;
@@ -130,6 +131,14 @@ void hfd_prep_destroy(hfd_prep* prep);
 int64_t hfd_prep_size(const hfd_prep* prep, const char* name);
 hfd_status hfd_prep_get(const hfd_prep* prep, const char* name, void* dst, int64_t count);
 hfd_status hfd_prep_set(hfd_prep* prep, const char* name, const void* src, int64_t count);
+
+/* Batches (many independent meshes advanced together): the disjoint union of n prep objects
+ * with identical physical and numerical options.  Member k's vertices (edges) follow those of
+ * members 0..k-1 in the input numbering of the result, so a batch state is the concatenation
+ * of the members' states.  The device mesh made from it runs every kernel once over all members
+ * and gives each member its own CFL time step (hfd_step with dt <= 0); hfd_last_dt then returns
+ * n values.  The inputs are not consumed.  Errors: HFD_ERR_ARG. */
+hfd_status hfd_prep_concat(const hfd_prep* const* preps, int32_t n, hfd_prep** out);
 
 /* ---------------------------------------------------------------- device mesh
  * hfd_mesh_create = hfd_prep_create + hfd_mesh_upload.  hfd_mesh_upload renumbers vertices
@@ -174,10 +183,10 @@ hfd_status hfd_steps_host(hfd_mesh* mesh, const double* U_in, double* U_out, dou
                           int32_t nsteps, void* stream);
 
 /* Same work as hfd_steps, launched kernel by kernel with CUDA events recorded around each
- * launch on `stream`; synchronises the stream and accumulates into kernel_ms[5] the time spent
+ * launch on `stream`; synchronises the stream and accumulates into kernel_ms[6] the time spent
  * in each kernel kind: [0] ghost refresh, [1] vertex fluxes, [2] edge interpolation + Riemann
- * flux, [3] divergence + RK stage, [4] time-step reduction.  Returns the launch count in
- * *launches.  Tracing aid: the events add a few microseconds per launch. */
+ * flux, [3] divergence + RK stage, [4] time-step reduction, [5] persistent stage kernel.
+ * Returns the launch count in *launches.  Tracing aid: events add a few microseconds each. */
 hfd_status hfd_steps_profiled(hfd_mesh* mesh, double* U, double dt, int32_t nsteps, void* stream,
                               double* kernel_ms, int64_t* launches);
 
@@ -197,7 +206,40 @@ hfd_status hfd_steps_profiled(hfd_mesh* mesh, double* U, double dt, int32_t nste
  * HFD_ERR_ARG (sizes, null pointers, mesh not on the current device), HFD_ERR_CUDA. */
 hfd_status hfd_residual_static(hfd_mesh* mesh, double* U, double* R, void* stream);
 
-/* dt used by the most recent step (synchronises the stream). */
+/* Discrete adjoint of one step (SURVEY config: gradients through the time stepping): given
+ * lam_np1 = dJ/dU_{n+1}, writes lam_n = (d hfd_step(U_n, dt) / d U_n)^T lam_np1, the exact
+ * vector-Jacobian product of the discrete step (Sec. 2.3: Alg. 1, Riemann flux, least-squares
+ * divergence, three-stage TVD Runge-Kutta) with the branch decisions of the sensor held fixed.
+ * The three stages are recomputed forward from U_n (not modified), then reversed; the
+ * divergence and stencil transposes are gathers over lists built on the first call, so the
+ * result is deterministic.  All arrays are 12*nv device arrays in internal order; dt > 0 is the
+ * fixed step of the forward step (a step with dt <= 0 depends on U_n through the CFL minimum,
+ * which this product does not differentiate).  FP64 meshes without ghost vertices or
+ * viscosity; other meshes get HFD_ERR_UNSUPPORTED.  Errors: HFD_ERR_ARG, HFD_ERR_CUDA. */
+hfd_status hfd_adjoint(hfd_mesh* mesh, const double* U_n, const double* lam_np1, double* lam_n,
+                       double dt, void* stream);
+
+/* How hfd_step runs a Runge-Kutta stage.  persistent = 0: four launches (ghost refresh, vertex
+ * fluxes, edge fluxes, divergence + stage update).  persistent = 1: one cooperative launch of
+ * `grid` blocks (0 = every co-resident block) running the same four phases separated by
+ * bounded grid barriers (a wait that exceeds its bound records HFD_ERR_TIMEOUT, see hfd_check).
+ * Both run the same per-entity code; they agree to rounding (the compiler may contract
+ * multiply-adds differently in the fused kernel).  Drops captured graphs.  Errors: HFD_ERR_ARG. */
+hfd_status hfd_mesh_set_launch(hfd_mesh* mesh, int32_t persistent, int32_t grid);
+
+/* Bound on the polls of one grid-barrier wait in the persistent launch (default 2^24 polls of
+ * at least 64 ns).  A smaller bound makes a stalled wait give up sooner: the kernel then records
+ * HFD_ERR_TIMEOUT in the error word and returns instead of waiting.  Drops captured graphs. */
+hfd_status hfd_mesh_set_barrier_limit(hfd_mesh* mesh, uint32_t polls);
+
+/* Autotuner: times one Runge-Kutta stage on (a copy of) the device state U, internal order,
+ * for the four-launch form and for the persistent form at every co-resident block count, keeps
+ * the fastest, and writes it to choice[0] (persistent) and choice[1] (grid) if choice is not
+ * NULL.  The choice changes the launch shape, not the method's arithmetic (results agree to
+ * rounding, see hfd_mesh_set_launch).  Synchronises. */
+hfd_status hfd_mesh_autotune(hfd_mesh* mesh, const double* U, void* stream, int32_t* choice);
+
+/* dt used by the most recent step, one value per member mesh (synchronises the stream). */
 hfd_status hfd_last_dt(hfd_mesh* mesh, double* dt, void* stream);
 
 /* Reads and clears the device error word (synchronises the stream): HFD_OK if clean, else the

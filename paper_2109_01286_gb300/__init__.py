@@ -6,5 +6,6 @@ in-tree library `_lib/libhfd.so` (host C++ preprocessing + CUDA kernels for sm_1
 """
 from . import hfd
 from .hfd import HfdError, Mesh, Prep, options
+from . import autograd
 
-__all__ = ["hfd", "HfdError", "Mesh", "Prep", "options"]
+__all__ = ["hfd", "autograd", "HfdError", "Mesh", "Prep", "options"]

@@ -26,11 +26,13 @@ def _nvcc():
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("prep.cpp", "kernels.cu", "api.cu", "noalloc.cu")]
+    return [os.path.join(CSRC, f) for f in ("prep.cpp", "kernels.cu", "api.cu", "noalloc.cu",
+                                            "adjoint.cu")]
 
 
 def _deps():
-    return _sources() + [os.path.join(CSRC, f) for f in ("prep.hpp", "kernels.hpp", "mesh.hpp")] + \
+    return _sources() + [os.path.join(CSRC, f) for f in ("prep.hpp", "kernels.hpp", "mesh.hpp",
+                                                         "adjoint_kernels.cuh")] + \
         [os.path.join(INCLUDE, "hfd.h"), os.path.abspath(__file__)]
 
 

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -164,29 +165,40 @@ hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
   d.Ef = (int)P.flux_edges.size();
   d.precision = m->opts.precision;
   d.viscous = P.opts.viscous;
-  // ---- vertex order: non-ghosts first, each part along a Hilbert curve
+  // ---- vertex order: non-ghosts first, then by member mesh (batches), each part along a
+  // Hilbert curve of the member's own bounding box
   m->perm.resize(V);
   {
-    double x0 = 0, x1 = P.Lx, y0 = 0, y1 = P.Ly;
-    if (!P.periodic_x || !(x1 > 0)) {
-      x0 = *std::min_element(P.x.begin(), P.x.end());
-      x1 = *std::max_element(P.x.begin(), P.x.end());
+    std::vector<double> box;
+    if (P.nmember > 1) {
+      box = P.member_box;
+    } else {
+      double x0 = 0, x1 = P.Lx, y0 = 0, y1 = P.Ly;
+      if (!P.periodic_x || !(x1 > 0)) {
+        x0 = *std::min_element(P.x.begin(), P.x.end());
+        x1 = *std::max_element(P.x.begin(), P.x.end());
+      }
+      if (!P.periodic_y || !(y1 > 0)) {
+        y0 = *std::min_element(P.y.begin(), P.y.end());
+        y1 = *std::max_element(P.y.begin(), P.y.end());
+      }
+      box = {x0, x1, y0, y1};
     }
-    if (!P.periodic_y || !(y1 > 0)) {
-      y0 = *std::min_element(P.y.begin(), P.y.end());
-      y1 = *std::max_element(P.y.begin(), P.y.end());
-    }
-    double sx = x1 > x0 ? 65535.0 / (x1 - x0) : 0, sy = y1 > y0 ? 65535.0 / (y1 - y0) : 0;
     std::vector<uint64_t> key(V);
     for (int v = 0; v < V; ++v) {
+      int mb = P.nmember > 1 ? P.member[v] : 0;
+      double x0 = box[4 * mb], x1 = box[4 * mb + 1], y0 = box[4 * mb + 2], y1 = box[4 * mb + 3];
+      double sx = x1 > x0 ? 65535.0 / (x1 - x0) : 0, sy = y1 > y0 ? 65535.0 / (y1 - y0) : 0;
       double xn = (P.x[v] - x0) * sx, yn = (P.y[v] - y0) * sy;
       uint32_t xi = (uint32_t)std::min(65535.0, std::max(0.0, xn));
       uint32_t yi = (uint32_t)std::min(65535.0, std::max(0.0, yn));
       key[v] = P.opts.renumber ? hilbert(xi, yi) : 0;
     }
     std::iota(m->perm.begin(), m->perm.end(), 0);
+    auto mem = [&](int v) { return P.nmember > 1 ? P.member[v] : 0; };
     std::stable_sort(m->perm.begin(), m->perm.end(), [&](int a, int b) {
       if (P.is_ghost[a] != P.is_ghost[b]) return P.is_ghost[a] < P.is_ghost[b];
+      if (mem(a) != mem(b)) return mem(a) < mem(b);
       if (key[a] != key[b]) return key[a] < key[b];
       return a < b;
     });
@@ -225,12 +237,27 @@ hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
   for (int i = 0; i < A; ++i) lmin[i] = P.lmin[m->perm[i]];
   TRY(dev_upload(m, (void**)&d.lmin, lmin));
   TRY(dev_upload(m, (void**)&m->dperm, m->perm));
-  TRY(dev_alloc(m, (void**)&d.dtbits, sizeof(unsigned long long)));
-  TRY(dev_alloc(m, (void**)&d.dt_last, sizeof(double)));
+  d.nmember = P.nmember;
+  TRY(dev_alloc(m, (void**)&d.dtbits, sizeof(unsigned long long) * d.nmember));
+  TRY(dev_alloc(m, (void**)&d.dt_last, sizeof(double) * d.nmember));
+  TRY(dev_alloc(m, (void**)&d.dtpartial, sizeof(double) * ((size_t)A / 256 + 1)));
   TRY(dev_alloc(m, (void**)&d.err, sizeof(unsigned)));
+  TRY(dev_alloc(m, (void**)&d.bar, 2 * sizeof(unsigned)));
+  if (d.nmember > 1) {
+    std::vector<int32_t> vm(A);
+    for (int i = 0; i < A; ++i) vm[i] = P.member[m->perm[i]];
+    TRY(dev_upload(m, (void**)&d.vmem, vm));
+  }
   TRY(dev_alloc(m, (void**)&m->U1, (size_t)12 * V * sizeof(double)));
   TRY(dev_alloc(m, (void**)&m->U2, (size_t)12 * V * sizeof(double)));
   CK(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+  // lanes per vertex in the divergence: FP64 is bound by the FP64 pipe and runs best without a
+  // cross-lane reduction (1); the FP32 path is bound by memory and prefers coalesced groups (4)
+  m->lanes = m->opts.precision == 0 ? 1 : 4;
+  if (const char* env = getenv("HFD_DIV_LANES")) {   // tuning override: 1, 2 or 4
+    int l = atoi(env);
+    if (l == 1 || l == 2 || l == 4) m->lanes = l;
+  }
   const hfd_options& o = P.opts;
   m->ph.gamma = o.gamma;
   m->ph.eps = o.weno_eps;
@@ -255,6 +282,7 @@ hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
   }
   for (int32_t r : P.rank) s.rank_hist[std::min(15, std::max(0, r))]++;
   s.div_degree_fallbacks = P.degree_fallbacks;
+  s.nmember = P.nmember;
   s.prep_seconds = P.prep_seconds;
   return HFD_OK;
 }
@@ -274,7 +302,7 @@ hfd_status residual_impl(hfd_mesh* m, double* U, double* R, cudaStream_t s) {
 // Optional per-kernel timing of the launches of a step (hfd_steps_profiled).
 struct Timer {
   cudaStream_t s;
-  double ms[5] = {0, 0, 0, 0, 0};
+  double ms[6] = {0, 0, 0, 0, 0, 0};
   int64_t launches = 0;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
 };
@@ -303,6 +331,20 @@ hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* t
   double* in[3] = {U, m->U1, m->U2};
   double* out[3] = {m->U1, m->U2, U};
   for (int k = 0; k < 3; ++k) {
+    if (m->persistent) {
+      int grid = m->grid;
+      if (grid <= 0) {
+        int per_sm = 0, nsm = 0;
+        CK(hfd::persistent_max_blocks(d, m->lanes, &per_sm, &nsm));
+        grid = std::max(1, per_sm) * nsm;
+      }
+      CK(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
+      CK(timed(5, [&] {
+        return hfd::launch_stage_persistent(d, in[k], U, out[k], hfd::DIV_STAGE, A_[k], B_[k], dt,
+                                            m->ph, m->lanes, grid, true, s);
+      }));
+      continue;
+    }
     if (d.G) CK(timed(0, [&] { return hfd::launch_ghost(d, in[k], s); }));
     CK(timed(1, [&] { return hfd::launch_vertex(d, in[k], m->ph, s); }));
     CK(timed(2, [&] { return hfd::launch_edge(d, m->ph, s); }));
@@ -313,6 +355,12 @@ hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* t
   }
   if (d.G) CK(timed(0, [&] { return hfd::launch_ghost(d, U, s); }));
   return HFD_OK;
+}
+
+void drop_graphs(hfd_mesh* m) {
+  for (auto& kv : m->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  m->graphs.clear();
 }
 
 }  // namespace
@@ -353,8 +401,7 @@ void hfd_mesh_destroy(hfd_mesh* m) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(m->device);
-  for (auto& kv : m->graphs)
-    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  drop_graphs(m);
   if (m->cap) cudaStreamDestroy(m->cap);
   for (void* p : m->allocs) cudaFree(p);
   cudaSetDevice(prev);
@@ -473,9 +520,88 @@ hfd_status hfd_steps_host(hfd_mesh* m, const double* U_in, double* U_out, double
   return HFD_OK;
 }
 
+hfd_status hfd_mesh_set_launch(hfd_mesh* m, int32_t persistent, int32_t grid) {
+  if (!m || persistent < 0 || persistent > 1 || grid < 0) {
+    set_error("hfd_mesh_set_launch: invalid argument");
+    return HFD_ERR_ARG;
+  }
+  if (persistent) {
+    int per_sm = 0, nsm = 0;
+    CK(hfd::persistent_max_blocks(m->dm, m->lanes, &per_sm, &nsm));
+    if (per_sm < 1 || grid > per_sm * nsm) {
+      set_error("hfd_mesh_set_launch: %d blocks exceed the %d co-resident blocks", grid, per_sm * nsm);
+      return HFD_ERR_ARG;
+    }
+  }
+  m->persistent = persistent;
+  m->grid = grid;
+  drop_graphs(m);
+  return HFD_OK;
+}
+
+hfd_status hfd_mesh_set_barrier_limit(hfd_mesh* m, uint32_t polls) {
+  if (!m) { set_error("hfd_mesh_set_barrier_limit: null mesh"); return HFD_ERR_ARG; }
+  m->dm.barrier_spins = polls;
+  drop_graphs(m);
+  return HFD_OK;
+}
+
+hfd_status hfd_mesh_autotune(hfd_mesh* m, const double* U, void* stream, int32_t* choice) {
+  if (!m || !U) { set_error("hfd_mesh_autotune: invalid argument"); return HFD_ERR_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevMesh& d = m->dm;
+  size_t bytes = (size_t)12 * d.V * sizeof(double);
+  CK(cudaMemcpyAsync(m->U1, U, bytes, cudaMemcpyDeviceToDevice, s));
+  int per_sm = 0, nsm = 0;
+  CK(hfd::persistent_max_blocks(d, m->lanes, &per_sm, &nsm));
+  struct Cand { int persistent, grid; };
+  std::vector<Cand> cands = {{0, 0}};
+  for (int b = 1; b <= per_sm; ++b) cands.push_back({1, b * nsm});
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  Cand pick = cands[0];
+  const double dt = 1e-12;   // any fixed step: the work does not depend on it
+  for (const Cand& c : cands) {
+    float tot = 0;
+    for (int rep = 0; rep < 4; ++rep) {
+      CK(cudaEventRecord(e0, s));
+      if (c.persistent) {
+        CK(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
+        CK(hfd::launch_stage_persistent(d, m->U1, m->U1, m->U2, hfd::DIV_STAGE, 0.0, 1.0, dt,
+                                        m->ph, m->lanes, c.grid, true, s));
+      } else {
+        if (d.G) CK(hfd::launch_ghost(d, m->U1, s));
+        CK(hfd::launch_vertex(d, m->U1, m->ph, s));
+        CK(hfd::launch_edge(d, m->ph, s));
+        CK(hfd::launch_div(d, m->U1, m->U1, m->U2, hfd::DIV_STAGE, 0.0, 1.0, dt, m->ph, m->lanes, s));
+      }
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) tot += ms;                  // the first repetition warms up
+    }
+    if (tot < best) { best = tot; pick = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  unsigned w = 0;                              // the trial stages must not leave an error
+  CK(cudaMemcpy(&w, d.err, sizeof w, cudaMemcpyDeviceToHost));
+  if (w & 4u) { set_error("hfd_mesh_autotune: a persistent trial timed out at a barrier"); return HFD_ERR_TIMEOUT; }
+  CK(cudaMemsetAsync(d.err, 0, sizeof(unsigned), s));
+  m->persistent = pick.persistent;
+  m->grid = pick.grid;
+  drop_graphs(m);
+  if (choice) { choice[0] = pick.persistent; choice[1] = pick.grid; }
+  return HFD_OK;
+}
+
 hfd_status hfd_last_dt(hfd_mesh* m, double* dt, void* stream) {
   if (!m || !dt) { set_error("hfd_last_dt: null argument"); return HFD_ERR_ARG; }
-  CK(cudaMemcpyAsync(dt, m->dm.dt_last, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaMemcpyAsync(dt, m->dm.dt_last, sizeof(double) * m->dm.nmember, cudaMemcpyDeviceToHost,
+                     (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return HFD_OK;
 }
@@ -488,6 +614,7 @@ hfd_status hfd_check(hfd_mesh* m, void* stream) {
   CK(cudaMemsetAsync(m->dm.err, 0, sizeof(unsigned), s));
   CK(cudaStreamSynchronize(s));
   if (w & 1u) { set_error("device error word: non-finite value"); return HFD_ERR_NONFINITE; }
+  if (w & 4u) { set_error("device error word: a grid barrier wait timed out"); return HFD_ERR_TIMEOUT; }
   if (w & 2u) { set_error("device error word: rho <= 0 after a stage"); return HFD_ERR_POSITIVITY; }
   return HFD_OK;
 }

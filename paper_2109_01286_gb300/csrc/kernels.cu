@@ -23,7 +23,7 @@
 
 namespace hfd {
 
-enum : unsigned { ERRBIT_NONFINITE = 1u, ERRBIT_POSITIVITY = 2u };
+enum : unsigned { ERRBIT_NONFINITE = 1u, ERRBIT_POSITIVITY = 2u, ERRBIT_TIMEOUT = 4u };
 
 // ------------------------------------------------------------------ vector loads
 __device__ __forceinline__ void ld12(const double* p, double* o) {
@@ -134,11 +134,20 @@ __device__ __forceinline__ void normal_flux(const T* w, T nx, T ny, T g1, T* f) 
 }
 
 // Roe's flux with Harten's entropy fix on all waves (Riemann flux, Sec. 2.3 after Alg. 1).
+// The primitive quantities of each side (1/rho, u, v, p, H) are formed once and shared by the
+// Roe average and the two normal fluxes.
 template <typename T>
 __device__ __forceinline__ void roe_flux(const T* wl, const T* wr, T nx, T ny, T g1, T harten,
                                          T* hq) {
-  T u, v, H, c;
-  roe_avg(wl, wr, g1, u, v, H, c);
+  T irl = T(1) / wl[0], irr = T(1) / wr[0];
+  T ul = wl[1] * irl, vl = wl[2] * irl, ur = wr[1] * irr, vr = wr[2] * irr;
+  T pl = g1 * (wl[3] - T(0.5) * (wl[1] * ul + wl[2] * vl));
+  T pr = g1 * (wr[3] - T(0.5) * (wr[1] * ur + wr[2] * vr));
+  T Hl = (wl[3] + pl) * irl, Hr = (wr[3] + pr) * irr;
+  T rl = sqrt(wl[0]), rr = sqrt(wr[0]);
+  T fl_ = rl / (rl + rr), fr_ = T(1) - fl_;
+  T u = fl_ * ul + fr_ * ur, v = fl_ * vl + fr_ * vr, H = fl_ * Hl + fr_ * Hr;
+  T c = sqrt(g1 * (H - T(0.5) * (u * u + v * v)));
   T L[4][4];
   left_ev(u, v, c, nx, ny, g1, L);
   T d[4] = {wr[0] - wl[0], wr[1] - wl[1], wr[2] - wl[2], wr[3] - wl[3]};
@@ -155,9 +164,9 @@ __device__ __forceinline__ void roe_flux(const T* wl, const T* wr, T nx, T ny, T
   }
   T diss[4];
   right_apply(u, v, H, c, nx, ny, k, diss);
-  T fl[4], fr[4];
-  normal_flux(wl, nx, ny, g1, fl);
-  normal_flux(wr, nx, ny, g1, fr);
+  T unl = ul * nx + vl * ny, unr = ur * nx + vr * ny;
+  T fl[4] = {wl[0] * unl, wl[1] * unl + pl * nx, wl[2] * unl + pl * ny, (wl[3] + pl) * unl};
+  T fr[4] = {wr[0] * unr, wr[1] * unr + pr * nx, wr[2] * unr + pr * ny, (wr[3] + pr) * unr};
 #pragma unroll
   for (int i = 0; i < 4; ++i) hq[i] = T(0.5) * (fl[i] + fr[i]) - T(0.5) * diss[i];
 }
@@ -177,9 +186,8 @@ __device__ __forceinline__ void smoothness(T u0, T u1, T u2, T u3, T u4, T* b) {
 
 // ------------------------------------------------------------------ k_vertex
 template <typename T, bool VISC>
-__global__ void __launch_bounds__(256) k_vertex(int V, const double* __restrict__ U, T* Ua, T* FG,
-                                                T* FGv, Phys ph) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void vertex_body(int v, int V, const double* __restrict__ U, T* Ua,
+                                            T* FG, T* FGv, const Phys& ph) {
   if (v >= V) return;
   double w[12];
 #pragma unroll
@@ -221,15 +229,52 @@ __global__ void __launch_bounds__(256) k_vertex(int V, const double* __restrict_
   }
 }
 
+template <typename T, bool VISC>
+__global__ void __launch_bounds__(256) k_vertex(int V, const double* __restrict__ U, T* Ua, T* FG,
+                                                T* FGv, Phys ph) {
+  vertex_body<T, VISC>(blockIdx.x * blockDim.x + threadIdx.x, V, U, Ua, FG, FGv, ph);
+}
+
 // ------------------------------------------------------------------ k_edge
 // One thread per flux edge.  Node order of the stencil: [i-2, i-1, i, i+1, i+2, i+3]; the left
 // state uses nodes 0..4, the right state nodes 1..5 with the WENO sub-stencils mirrored.
+//
+// Arithmetic layout (same values as Alg. 1, fewer operations in the bulk type T):
+//  * The 5-node value of every characteristic component is L times the same 5-node combination
+//    of the conservative data (L is shared by all nodes), and R L = I.  So a side whose four
+//    components all take the 5-node branch is the 5-node combination in conservative
+//    variables, W5, with no projection and no back-projection.
+//  * The discontinuity sensor needs only differences of characteristic values (the
+//    smoothness indicators are shift-invariant).  They are formed from w_k - w_i, rounded to
+//    FP32 and projected with an FP32 L; the test 0.01 < omega_1 < 0.79 is evaluated in that
+//    precision with a relative guard band.  Decisions inside the band are re-taken with
+//    characteristic values and weights in T / FP64, so every decision equals the one made in
+//    the path's own precision.
+//  * Only sides with a 3-node (or re-taken) component project W5, recompute the characteristic
+//    values of that component, form the omega-weighted candidates and back-project.
+constexpr float kGuard = 1e-3f;
+
+__device__ __forceinline__ float sensor_diff(double a, double b) { return (float)(a - b); }
+__device__ __forceinline__ float sensor_diff(float a, float b) { return a - b; }
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_edge(int Ef, const int32_t* __restrict__ sten,
-                                              const T* __restrict__ nrm, const T* __restrict__ w5,
-                                              const T* __restrict__ w3, const T* __restrict__ Ua,
-                                              T* __restrict__ h, Phys ph, unsigned* err) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sensor64(T u0, T u1, T u2, T u3, T u4, const Phys& ph,
+                                         double* t, double& S) {
+  T b[3];
+  smoothness(u0, u1, u2, u3, u4, b);
+  double s0 = ph.eps + (double)b[0], s1 = ph.eps + (double)b[1], s2 = ph.eps + (double)b[2];
+  s0 *= s0; s1 *= s1; s2 *= s2;
+  t[0] = (1.0 / 16.0) * s1 * s2;
+  t[1] = (10.0 / 16.0) * s0 * s2;
+  t[2] = (5.0 / 16.0) * s0 * s1;
+  S = t[0] + t[1] + t[2];
+}
+
+template <typename T>
+__device__ __forceinline__ void edge_body(int e, int Ef, const int32_t* __restrict__ sten,
+                                          const T* __restrict__ nrm, const T* __restrict__ w5,
+                                          const T* __restrict__ w3, const T* __restrict__ Ua,
+                                          T* __restrict__ h, const Phys& ph) {
   if (e >= Ef) return;
   const T g1 = T(ph.gamma - 1.0);
   int s[6];
@@ -244,70 +289,105 @@ __global__ void __launch_bounds__(128) k_edge(int Ef, const int32_t* __restrict_
     ld12(Ua + (size_t)s[3] * 12, a);
     wj[0] = a[0]; wj[1] = a[1]; wj[2] = a[2]; wj[3] = a[3];
   }
-  T u, v, H, c;
-  roe_avg(wi, wj, g1, u, v, H, c);
-  T L[4][4];
-  left_ev(u, v, c, nx, ny, g1, L);
-  // characteristic values of the 6 nodes and the 5-node Hermite sums of both sides
-  T cv[6][4];
-  T C5L[4] = {T(0), T(0), T(0), T(0)}, C5R[4] = {T(0), T(0), T(0), T(0)};
+  // FP32 left eigenvectors at the Roe state of the edge ends (sensor only)
+  float Lf[4][4];
+  {
+    float fi[4] = {(float)wi[0], (float)wi[1], (float)wi[2], (float)wi[3]};
+    float fj[4] = {(float)wj[0], (float)wj[1], (float)wj[2], (float)wj[3]};
+    float u, v, H, c;
+    roe_avg(fi, fj, (float)g1, u, v, H, c);
+    left_ev(u, v, c, (float)nx, (float)ny, (float)g1, Lf);
+  }
+  T W5L[4] = {T(0), T(0), T(0), T(0)}, W5R[4] = {T(0), T(0), T(0), T(0)};
+  float cf[6][4];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     T a[12];
     ld12(Ua + (size_t)s[k] * 12, a);
-    T wlv = T(0), wlx = T(0), wly = T(0), wrv = T(0), wrx = T(0), wry = T(0);
     if (k <= 4) {
-      wlv = __ldg(w5 + (size_t)(3 * k) * Ef + e);
-      wlx = __ldg(w5 + (size_t)(3 * k + 1) * Ef + e);
-      wly = __ldg(w5 + (size_t)(3 * k + 2) * Ef + e);
+      T wv = __ldg(w5 + (size_t)(3 * k) * Ef + e), wx = __ldg(w5 + (size_t)(3 * k + 1) * Ef + e);
+      T wy = __ldg(w5 + (size_t)(3 * k + 2) * Ef + e);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) W5L[r] = fma(wv, a[r], fma(wx, a[4 + r], fma(wy, a[8 + r], W5L[r])));
     }
     if (k >= 1) {
-      wrv = __ldg(w5 + (size_t)(15 + 3 * (k - 1)) * Ef + e);
-      wrx = __ldg(w5 + (size_t)(16 + 3 * (k - 1)) * Ef + e);
-      wry = __ldg(w5 + (size_t)(17 + 3 * (k - 1)) * Ef + e);
+      T wv = __ldg(w5 + (size_t)(15 + 3 * (k - 1)) * Ef + e);
+      T wx = __ldg(w5 + (size_t)(16 + 3 * (k - 1)) * Ef + e);
+      T wy = __ldg(w5 + (size_t)(17 + 3 * (k - 1)) * Ef + e);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) W5R[r] = fma(wv, a[r], fma(wx, a[4 + r], fma(wy, a[8 + r], W5R[r])));
     }
+    // end-state differences rounded once to FP32 (for FP32 data the float subtraction is that
+    // correctly rounded difference already; for FP64 data it is formed in FP64 first)
+    float d[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) d[r] = sensor_diff(a[r], wi[r]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      cf[k][q] = Lf[q][0] * d[0] + Lf[q][1] * d[1] + Lf[q][2] * d[2] + Lf[q][3] * d[3];
+  }
+  // sensor in FP32: bit (side*4+q) of `rough` = 3-node branch, of `amb` = inside the guard band
+  unsigned rough = 0, amb = 0;
+#pragma unroll
+  for (int side = 0; side < 2; ++side)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      T c0 = L[q][0] * a[0] + L[q][1] * a[1] + L[q][2] * a[2] + L[q][3] * a[3];
-      T cx = L[q][0] * a[4] + L[q][1] * a[5] + L[q][2] * a[6] + L[q][3] * a[7];
-      T cy = L[q][0] * a[8] + L[q][1] * a[9] + L[q][2] * a[10] + L[q][3] * a[11];
-      cv[k][q] = c0;
-      if (k <= 4) C5L[q] += wlv * c0 + wlx * cx + wly * cy;
-      if (k >= 1) C5R[q] += wrv * c0 + wrx * cx + wry * cy;
+      float u0, u1, u2, u3, u4;
+      if (side == 0) { u0 = cf[0][q]; u1 = cf[1][q]; u2 = cf[2][q]; u3 = cf[3][q]; u4 = cf[4][q]; }
+      else           { u0 = cf[5][q]; u1 = cf[4][q]; u2 = cf[3][q]; u3 = cf[2][q]; u4 = cf[1][q]; }
+      float b[3];
+      smoothness(u0, u1, u2, u3, u4, b);
+      float eps = (float)ph.eps;
+      float s0 = eps + b[0], s1 = eps + b[1], s2 = eps + b[2];
+      s0 *= s0; s1 *= s1; s2 *= s2;
+      float t0 = 0.0625f * s1 * s2, t1 = 0.625f * s0 * s2, t2 = 0.3125f * s0 * s1;
+      float S = t0 + t1 + t2;
+      float mlo = t0 - (float)ph.sens_lo * S, mhi = (float)ph.sens_hi * S - t0;
+      unsigned bit = 1u << (side * 4 + q);
+      if (!(mlo > 0.f && mhi > 0.f)) rough |= bit;
+      if (!(fabsf(mlo) > kGuard * S && fabsf(mhi) > kGuard * S)) amb |= bit;
     }
-  }
   T wside[2][4];
 #pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    T C[4];
+  for (int r = 0; r < 4; ++r) { wside[0][r] = W5L[r]; wside[1][r] = W5R[r]; }
+  if (rough | amb) {
+    T u, v, H, c;
+    roe_avg(wi, wj, g1, u, v, H, c);
+    T L[4][4];
+    left_ev(u, v, c, nx, ny, g1, L);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      T u0, u1, u2, u3, u4;
-      if (side == 0) { u0 = cv[0][q]; u1 = cv[1][q]; u2 = cv[2][q]; u3 = cv[3][q]; u4 = cv[4][q]; }
-      else           { u0 = cv[5][q]; u1 = cv[4][q]; u2 = cv[3][q]; u3 = cv[2][q]; u4 = cv[1][q]; }
-      T b[3];
-      smoothness(u0, u1, u2, u3, u4, b);
-      // omega_j = (d_j / s_j^2) / sum, s_j = eps + beta_j; with t_j = d_j prod_{k != j} s_k^2
-      // the sensor test 0.01 < omega_1 < 0.79 needs no division (FP64, R20)
-      double s0 = ph.eps + (double)b[0], s1 = ph.eps + (double)b[1], s2 = ph.eps + (double)b[2];
-      s0 *= s0; s1 *= s1; s2 *= s2;
-      double t0 = (1.0 / 16.0) * s1 * s2, t1 = (10.0 / 16.0) * s0 * s2, t2 = (5.0 / 16.0) * s0 * s1;
-      double S = t0 + t1 + t2;
-      bool smooth = (t0 > ph.sens_lo * S) && (t0 < ph.sens_hi * S);
-      if (smooth) {
-        C[q] = side == 0 ? C5L[q] : C5R[q];
-      } else {
+    for (int side = 0; side < 2; ++side) {
+      unsigned mine = ((rough | amb) >> (side * 4)) & 15u;
+      if (!mine) continue;
+      const T* W5 = side == 0 ? W5L : W5R;
+      T C[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        C[q] = L[q][0] * W5[0] + L[q][1] * W5[1] + L[q][2] * W5[2] + L[q][3] * W5[3];
+        if (!((mine >> q) & 1u)) continue;
+        T cq[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          int k = side == 0 ? j : 5 - j;
+          T a[4];
+          ld4(Ua + (size_t)s[k] * 12, a);
+          cq[j] = L[q][0] * a[0] + L[q][1] * a[1] + L[q][2] * a[2] + L[q][3] * a[3];
+        }
+        double t[3], S;
+        sensor64(cq[0], cq[1], cq[2], cq[3], cq[4], ph, t, S);
+        bool smooth = (t[0] > ph.sens_lo * S) && (t[0] < ph.sens_hi * S);
+        if (smooth) continue;
         const T* w = w3 + (size_t)(9 * side) * Ef + e;
-        T c1 = __ldg(w) * u0 + __ldg(w + Ef) * u1 + __ldg(w + 2 * (size_t)Ef) * u2;
-        T c2 = __ldg(w + 3 * (size_t)Ef) * u1 + __ldg(w + 4 * (size_t)Ef) * u2 +
-               __ldg(w + 5 * (size_t)Ef) * u3;
-        T c3 = __ldg(w + 6 * (size_t)Ef) * u2 + __ldg(w + 7 * (size_t)Ef) * u3 +
-               __ldg(w + 8 * (size_t)Ef) * u4;
+        T c1 = __ldg(w) * cq[0] + __ldg(w + Ef) * cq[1] + __ldg(w + 2 * (size_t)Ef) * cq[2];
+        T c2 = __ldg(w + 3 * (size_t)Ef) * cq[1] + __ldg(w + 4 * (size_t)Ef) * cq[2] +
+               __ldg(w + 5 * (size_t)Ef) * cq[3];
+        T c3 = __ldg(w + 6 * (size_t)Ef) * cq[2] + __ldg(w + 7 * (size_t)Ef) * cq[3] +
+               __ldg(w + 8 * (size_t)Ef) * cq[4];
         double iS = 1.0 / S;
-        C[q] = T((t0 * (double)c1 + t1 * (double)c2 + t2 * (double)c3) * iS);
+        C[q] = T((t[0] * (double)c1 + t[1] * (double)c2 + t[2] * (double)c3) * iS);
       }
+      right_apply(u, v, H, c, nx, ny, C, wside[side]);
     }
-    right_apply(u, v, H, c, nx, ny, C, wside[side]);
   }
   // positivity (R16): fall back to the end state of that side
   if (!(wside[0][0] > T(0)) || !(pressure(wside[0], g1) > T(0)))
@@ -321,23 +401,68 @@ __global__ void __launch_bounds__(128) k_edge(int Ef, const int32_t* __restrict_
   st4(h + (size_t)e * 4, hq);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) k_edge(int Ef, const int32_t* __restrict__ sten,
+                                              const T* __restrict__ nrm, const T* __restrict__ w5,
+                                              const T* __restrict__ w3, const T* __restrict__ Ua,
+                                              T* __restrict__ h, Phys ph) {
+  edge_body<T>(blockIdx.x * blockDim.x + threadIdx.x, Ef, sten, nrm, w5, w3, Ua, h, ph);
+}
+
 // ------------------------------------------------------------------ k_div
-// G lanes per active vertex; lanes stride over the CSR entries; fixed xor-butterfly
-// reduction.  acc = div(f) - div(f_vis) for the 12 rows; R = -acc.
+// G lanes per active vertex (G in {1, 2, 4}); lanes stride over the CSR entries; the 12 partial
+// sums are combined by a fixed reduce-scatter over the group (each level halves the values a
+// lane holds), so the result is deterministic and every add is useful.  acc = div(f) -
+// div(f_vis) for the 12 rows; R = -acc.
+template <int G, typename T>
+__device__ __forceinline__ void reduce_scatter12(T* acc, int lane) {
+  // after the loop lane `lane` holds rows base .. base + 12/G - 1 in acc[0 .. 12/G - 1]
+  if (G >= 2) {
+    const int o = G / 2;
+    bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      T keep = hi ? acc[6 + i] : acc[i];
+      T send = hi ? acc[i] : acc[6 + i];
+      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o, G);
+    }
+  }
+  if (G >= 4) {
+    bool hi = (lane & 1) != 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T keep = hi ? acc[3 + i] : acc[i];
+      T send = hi ? acc[i] : acc[3 + i];
+      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1, G);
+    }
+  }
+}
+
+// Per-stage arguments of the divergence: out = R (residual) or a*Un + b*(Us + dt*R) (stage).
+struct StageArgs {
+  const double* Us;
+  const double* Un;
+  double* out;
+  int mode;
+  double a, b, dt_fixed;
+};
+
 template <typename T, int G, bool VISC>
-__global__ void __launch_bounds__(256) k_div(int A, int V, const int32_t* __restrict__ vptr,
-                                             const int32_t* __restrict__ vidx,
-                                             const int32_t* __restrict__ eptr,
-                                             const int32_t* __restrict__ eidx,
-                                             const T* __restrict__ cv, const T* __restrict__ ce,
-                                             const T* __restrict__ cvis, const T* __restrict__ FG,
-                                             const T* __restrict__ FGv, const T* __restrict__ h,
-                                             const double* __restrict__ Us,
-                                             const double* __restrict__ Un, double* out, int mode,
-                                             double a, double b, double dt_fixed,
-                                             const unsigned long long* dtbits, double cfl,
-                                             double* dt_last, unsigned* err) {
-  int gt = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __restrict__ vptr,
+                                         const int32_t* __restrict__ vidx,
+                                         const int32_t* __restrict__ eptr,
+                                         const int32_t* __restrict__ eidx,
+                                         const T* __restrict__ cv, const T* __restrict__ ce,
+                                         const T* __restrict__ cvis, const T* __restrict__ FG,
+                                         const T* __restrict__ FGv, const T* __restrict__ h,
+                                         const StageArgs& sa, const int32_t* __restrict__ vmem,
+                                         const unsigned long long* dtbits, double cfl,
+                                         double* dt_last, unsigned* err) {
+  const double* __restrict__ Us = sa.Us;
+  const double* __restrict__ Un = sa.Un;
+  double* out = sa.out;
+  const int mode = sa.mode;
+  const double a = sa.a, b = sa.b, dt_fixed = sa.dt_fixed;
   int r = gt / G, lane = gt % G;
   bool live = r < A;
   T acc[12];
@@ -355,9 +480,9 @@ __global__ void __launch_bounds__(256) k_div(int A, int V, const int32_t* __rest
       T cxg = __ldg(c + 3 * N + j), cyf = __ldg(c + 4 * N + j), cyg = __ldg(c + 5 * N + j);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        acc[q] += c0f * f[q] + c0g * f[4 + q];
-        acc[4 + q] += cxf * f[q] + cxg * f[4 + q];
-        acc[8 + q] += cyf * f[q] + cyg * f[4 + q];
+        acc[q] = fma(c0g, f[4 + q], fma(c0f, f[q], acc[q]));
+        acc[4 + q] = fma(cxg, f[4 + q], fma(cxf, f[q], acc[4 + q]));
+        acc[8 + q] = fma(cyg, f[4 + q], fma(cyf, f[q], acc[8 + q]));
       }
       if (VISC) {
         ld8(FGv + (size_t)uu * 8, f);
@@ -365,9 +490,9 @@ __global__ void __launch_bounds__(256) k_div(int A, int V, const int32_t* __rest
         cxg = __ldg(cz + 3 * N + j); cyf = __ldg(cz + 4 * N + j); cyg = __ldg(cz + 5 * N + j);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          acc[q] -= c0f * f[q] + c0g * f[4 + q];
-          acc[4 + q] -= cxf * f[q] + cxg * f[4 + q];
-          acc[8 + q] -= cyf * f[q] + cyg * f[4 + q];
+          acc[q] = fma(-c0g, f[4 + q], fma(-c0f, f[q], acc[q]));
+          acc[4 + q] = fma(-cxg, f[4 + q], fma(-cxf, f[q], acc[4 + q]));
+          acc[8 + q] = fma(-cyg, f[4 + q], fma(-cyf, f[q], acc[8 + q]));
         }
       }
     }
@@ -380,43 +505,66 @@ __global__ void __launch_bounds__(256) k_div(int A, int V, const int32_t* __rest
       T d0 = __ldg(d + j), dx = __ldg(d + M + j), dy = __ldg(d + 2 * M + j);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        acc[q] += d0 * hv[q];
-        acc[4 + q] += dx * hv[q];
-        acc[8 + q] += dy * hv[q];
+        acc[q] = fma(d0, hv[q], acc[q]);
+        acc[4 + q] = fma(dx, hv[q], acc[4 + q]);
+        acc[8 + q] = fma(dy, hv[q], acc[8 + q]);
       }
     }
   }
-#pragma unroll
-  for (int off = G / 2; off > 0; off >>= 1)
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off, G);
+  reduce_scatter12<G>(acc, lane);
   if (!live) return;
-  double dt = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)*dtbits);
-  if (mode == DIV_STAGE && gt == 0 && dt_last) *dt_last = dt;
+  // time step of this vertex's mesh (a batch holds several meshes, each with its own CFL step)
+  const int mem = vmem ? __ldg(vmem + r) : 0;
+  double dt = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)dtbits[mem]);
+  if (mode == DIV_STAGE && lane == 0 && dt_last && (r == 0 || (vmem && __ldg(vmem + r - 1) != mem)))
+    dt_last[mem] = dt;
+  const int per = 12 / G;
+  const int base = (G >= 2 && (lane & (G / 2)) ? 6 : 0) + (G >= 4 && (lane & 1) ? 3 : 0);
   unsigned bad = 0;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    if (k % G != lane) continue;
-    double R = -(double)acc[k];
-    size_t i = (size_t)k * V + r;
+  for (int i = 0; i < per; ++i) {
+    int k = base + i;
+    double R = -(double)acc[i];
+    size_t idx = (size_t)k * V + r;
     double o;
     if (mode == DIV_RESIDUAL) {
       o = R;
     } else {
-      o = b * (Us[i] + dt * R);
-      if (a != 0.0) o += a * Un[i];   // the first stage does not read the base state
+      o = b * (Us[idx] + dt * R);
+      if (a != 0.0) o += a * Un[idx];   // the first stage does not read the base state
     }
-    out[i] = o;
+    out[idx] = o;
     if (!isfinite(o)) bad |= ERRBIT_NONFINITE;
     if (mode == DIV_STAGE && k == 0 && !(o > 0.0)) bad |= ERRBIT_POSITIVITY;
   }
   if (bad) atomicOr(err, bad);
 }
 
+// FP32 data: memory-latency bound, so at least 4 resident blocks of 256 threads per SM; FP64
+// data: FP64-pipe bound, no occupancy constraint.
+template <typename T>
+struct DivOcc { static constexpr int kMinBlocks = 1; };
+template <>
+struct DivOcc<float> { static constexpr int kMinBlocks = 4; };
+
+template <typename T, int G, bool VISC>
+__global__ void __launch_bounds__(256, DivOcc<T>::kMinBlocks) k_div(int A, int V, const int32_t* __restrict__ vptr,
+                                             const int32_t* __restrict__ vidx,
+                                             const int32_t* __restrict__ eptr,
+                                             const int32_t* __restrict__ eidx,
+                                             const T* __restrict__ cv, const T* __restrict__ ce,
+                                             const T* __restrict__ cvis, const T* __restrict__ FG,
+                                             const T* __restrict__ FGv, const T* __restrict__ h,
+                                             StageArgs sa, const int32_t* __restrict__ vmem,
+                                             const unsigned long long* dtbits, double cfl,
+                                             double* dt_last, unsigned* err) {
+  div_body<T, G, VISC>(blockIdx.x * blockDim.x + threadIdx.x, A, V, vptr, vidx, eptr, eidx, cv,
+                       ce, cvis, FG, FGv, h, sa, vmem, dtbits, cfl, dt_last, err);
+}
+
 // ------------------------------------------------------------------ small kernels
-__global__ void k_ghost(int Gn, int V, const int32_t* gid, const int32_t* gdonor,
-                        const int32_t* gflags, double* U) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void ghost_body(int g, int Gn, int V, const int32_t* gid,
+                                           const int32_t* gdonor, const int32_t* gflags, double* U) {
   if (g >= Gn) return;
   int t = gid[g], d = gdonor[g], f = gflags[g];
 #pragma unroll
@@ -427,10 +575,24 @@ __global__ void k_ghost(int Gn, int V, const int32_t* gid, const int32_t* gdonor
   }
 }
 
-// min over active vertices of l_min / (|u| + c) (R12), reduced by warp shuffles and an
-// atomicMin on the bit pattern (positive doubles order like their bits): order-independent.
-__global__ void k_dtmin(int A, int V, const double* __restrict__ U, const double* __restrict__ lmin,
-                        double gamma, unsigned long long* bits) {
+__global__ void k_ghost(int Gn, int V, const int32_t* gid, const int32_t* gdonor,
+                        const int32_t* gflags, double* U) {
+  ghost_body(blockIdx.x * blockDim.x + threadIdx.x, Gn, V, gid, gdonor, gflags, U);
+}
+
+// min over the active vertices of each mesh of l_min / (|u| + c) (R12), in two passes without
+// contention on one address.  Pass 1: each block of 256 vertices reduces through warp shuffles
+// and shared memory; a block inside one mesh writes its minimum to partial[block], a block that
+// straddles meshes (batches only) updates the meshes' minima directly with atomicMin.  Pass 2:
+// one block reduces the partial minima; if they all belong to one mesh (always, for a single
+// mesh) with one atomicMin, else each thread scans a contiguous run of blocks and issues one
+// atomicMin per mesh it meets.  Positive doubles order like their bit patterns, so the result
+// does not depend on the order of the atomics.
+__global__ void __launch_bounds__(256) k_dtmin(int A, int V, const double* __restrict__ U,
+                                               const double* __restrict__ lmin,
+                                               const int32_t* __restrict__ vmem, double gamma,
+                                               unsigned long long* bits, double* partial) {
+  __shared__ double wmin[8];
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   double val = INFINITY;
   if (v < A) {
@@ -441,10 +603,62 @@ __global__ void k_dtmin(int A, int V, const double* __restrict__ U, const double
     val = lmin[v] / s;
     if (!(val > 0.0)) val = INFINITY;   // non-physical states do not set the step
   }
+  int first = blockIdx.x * blockDim.x, last = min(A - 1, first + (int)blockDim.x - 1);
+  bool uniform = !vmem || vmem[first] == vmem[last];
+  if (!uniform) {
+    if (threadIdx.x == 0) partial[blockIdx.x] = INFINITY;
+    int mem = v < A ? vmem[v] : -1;
+    if (mem >= 0 && val < INFINITY) atomicMin(bits + mem, (unsigned long long)__double_as_longlong(val));
+    return;
+  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, off));
-  if ((threadIdx.x & 31) == 0 && val < INFINITY)
-    atomicMin(bits, (unsigned long long)__double_as_longlong(val));
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = val;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    val = threadIdx.x < (blockDim.x >> 5) ? wmin[threadIdx.x] : INFINITY;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, off));
+    if (threadIdx.x == 0) partial[blockIdx.x] = val;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_dtmin_final(int nblk, int A, const int32_t* __restrict__ vmem,
+                                                      const double* __restrict__ partial,
+                                                      unsigned long long* bits) {
+  __shared__ double wmin[32];
+  const int bs = 256;                                       // vertices per pass-1 block
+  bool one_mesh = !vmem || vmem[0] == vmem[A - 1];
+  if (one_mesh) {
+    double val = INFINITY;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) val = fmin(val, partial[i]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, off));
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = val;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      val = threadIdx.x < (blockDim.x >> 5) ? wmin[threadIdx.x] : INFINITY;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, off));
+      if (threadIdx.x == 0 && val < INFINITY)
+        atomicMin(bits + (vmem ? vmem[0] : 0), (unsigned long long)__double_as_longlong(val));
+    }
+    return;
+  }
+  int per = (nblk + blockDim.x - 1) / blockDim.x;
+  int b0 = threadIdx.x * per, b1 = min(nblk, b0 + per);
+  int cur = -1;
+  double val = INFINITY;
+  for (int b = b0; b < b1; ++b) {
+    int mem = vmem[b * bs];
+    if (mem != cur) {
+      if (cur >= 0 && val < INFINITY) atomicMin(bits + cur, (unsigned long long)__double_as_longlong(val));
+      cur = mem;
+      val = INFINITY;
+    }
+    val = fmin(val, partial[b]);
+  }
+  if (cur >= 0 && val < INFINITY) atomicMin(bits + cur, (unsigned long long)__double_as_longlong(val));
 }
 
 __global__ void k_permute(int V, const int32_t* __restrict__ perm, const double* __restrict__ src,
@@ -459,8 +673,86 @@ __global__ void k_permute(int V, const int32_t* __restrict__ perm, const double*
   }
 }
 
+// ------------------------------------------------------------------ persistent stage kernel
+// One cooperative launch per Runge-Kutta stage: ghost refresh, vertex fluxes, edge fluxes and
+// divergence + stage update run as phases of one grid, separated by grid-wide barriers.  The
+// launch is cooperative, so all blocks are resident.  Every barrier wait is bounded: a block that
+// waits longer than kBarrierSpins polls records HFD_ERR_TIMEOUT in the error word and leaves the
+// kernel, and the blocks waiting for it at later barriers time out in turn, so the kernel always
+// ends.  Each phase runs the same per-entity code as the separate kernels (results agree with the
+// four-launch path to rounding: multiply-adds may be contracted differently when fused).  The poll bound is a launch argument (default 2^24 polls of
+// >= 64 ns, i.e. about a second or more).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err,
+                                             unsigned max_spins) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* gen = bar + 1;
+    unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*gen == g) {
+        if (++spins > max_spins) {
+          atomicOr(err, ERRBIT_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T, int G, bool VISC>
+__global__ void __launch_bounds__(128) k_stage(KernelArgs ka, StageArgs sa, Phys ph, int do_ghost) {
+  const unsigned nb = gridDim.x;
+  const int stride = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  double* U = const_cast<double*>(sa.Us);
+  if (do_ghost) {
+    for (int g = tid; g < ka.G; g += stride)
+      ghost_body(g, ka.G, ka.V, ka.gid, ka.gdonor, ka.gflags, U);
+    if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
+  }
+  for (int v = tid; v < ka.V; v += stride)
+    vertex_body<T, VISC>(v, ka.V, sa.Us, (T*)ka.Ua, (T*)ka.FG, (T*)ka.FGv, ph);
+  if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
+  for (int e = tid; e < ka.Ef; e += stride)
+    edge_body<T>(e, ka.Ef, ka.sten, (const T*)ka.nrm, (const T*)ka.w5, (const T*)ka.w3,
+                 (const T*)ka.Ua, (T*)ka.h, ph);
+  if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
+  // every lane of a warp runs the same number of iterations (shuffles inside div_body)
+  const long long total = (long long)ka.A * G;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride)
+    div_body<T, G, VISC>((int)(base + threadIdx.x), ka.A, ka.V, ka.vptr, ka.vidx, ka.eptr, ka.eidx,
+                         (const T*)ka.cv, (const T*)ka.ce, (const T*)ka.cvis, (const T*)ka.FG,
+                         (const T*)ka.FGv, (const T*)ka.h, sa, ka.vmem, ka.dtbits, ph.cfl,
+                         ka.dt_last, ka.err);
+}
+
 // ------------------------------------------------------------------ launchers
 static inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
+
+KernelArgs kernel_args(const DevMesh& m) {
+  KernelArgs a;
+  a.V = m.V; a.A = m.A; a.Ef = m.Ef; a.G = m.G;
+  a.sten = m.sten; a.vptr = m.vptr; a.vidx = m.vidx; a.eptr = m.eptr; a.eidx = m.eidx;
+  a.gid = m.gid; a.gdonor = m.gdonor; a.gflags = m.gflags; a.vmem = m.vmem;
+  a.nrm = m.nrm; a.w5 = m.w5; a.w3 = m.w3; a.cv = m.cv; a.ce = m.ce; a.cvis = m.cvis;
+  a.Ua = m.Ua; a.FG = m.FG; a.FGv = m.FGv; a.h = m.h;
+  a.dtbits = m.dtbits; a.dt_last = m.dt_last; a.err = m.err; a.bar = m.bar;
+  a.spins = m.barrier_spins;
+  return a;
+}
 
 cudaError_t launch_ghost(const DevMesh& m, double* U, cudaStream_t s) {
   if (m.G == 0) return cudaSuccess;
@@ -490,57 +782,103 @@ cudaError_t launch_edge(const DevMesh& m, const Phys& ph, cudaStream_t s) {
   int nb = blocks(m.Ef, 128);
   if (m.precision == 0)
     k_edge<double><<<nb, 128, 0, s>>>(m.Ef, m.sten, (const double*)m.nrm, (const double*)m.w5,
-                                      (const double*)m.w3, (const double*)m.Ua, (double*)m.h, ph,
-                                      m.err);
+                                      (const double*)m.w3, (const double*)m.Ua, (double*)m.h, ph);
   else
     k_edge<float><<<nb, 128, 0, s>>>(m.Ef, m.sten, (const float*)m.nrm, (const float*)m.w5,
-                                     (const float*)m.w3, (const float*)m.Ua, (float*)m.h, ph, m.err);
+                                     (const float*)m.w3, (const float*)m.Ua, (float*)m.h, ph);
   return cudaGetLastError();
 }
 
 template <typename T, int G>
-static void div_dispatch(const DevMesh& m, const double* Us, const double* Un, double* out,
-                         int mode, double a, double b, double dt_fixed, const Phys& ph,
-                         cudaStream_t s) {
+static void div_dispatch(const DevMesh& m, const StageArgs& sa, const Phys& ph, cudaStream_t s) {
   long long threads = (long long)m.A * G;
   int nb = blocks(threads, 256);
   if (m.viscous)
     k_div<T, G, true><<<nb, 256, 0, s>>>(m.A, m.V, m.vptr, m.vidx, m.eptr, m.eidx, (const T*)m.cv,
                                          (const T*)m.ce, (const T*)m.cvis, (const T*)m.FG,
-                                         (const T*)m.FGv, (const T*)m.h, Us, Un, out, mode, a, b,
-                                         dt_fixed, m.dtbits, ph.cfl, m.dt_last, m.err);
+                                         (const T*)m.FGv, (const T*)m.h, sa, m.vmem, m.dtbits,
+                                         ph.cfl, m.dt_last, m.err);
   else
     k_div<T, G, false><<<nb, 256, 0, s>>>(m.A, m.V, m.vptr, m.vidx, m.eptr, m.eidx,
                                           (const T*)m.cv, (const T*)m.ce, nullptr, (const T*)m.FG,
-                                          nullptr, (const T*)m.h, Us, Un, out, mode, a, b, dt_fixed,
-                                          m.dtbits, ph.cfl, m.dt_last, m.err);
+                                          nullptr, (const T*)m.h, sa, m.vmem, m.dtbits, ph.cfl,
+                                          m.dt_last, m.err);
 }
 
 cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, double* out, int mode,
                        double a, double b, double dt_fixed, const Phys& ph, int lanes,
                        cudaStream_t s) {
   if (m.A == 0) return cudaSuccess;
+  StageArgs sa{Us, Un, out, mode, a, b, dt_fixed};
   if (m.precision == 0) {
     switch (lanes) {
-      case 4: div_dispatch<double, 4>(m, Us, Un, out, mode, a, b, dt_fixed, ph, s); break;
-      case 16: div_dispatch<double, 16>(m, Us, Un, out, mode, a, b, dt_fixed, ph, s); break;
-      default: div_dispatch<double, 8>(m, Us, Un, out, mode, a, b, dt_fixed, ph, s); break;
+      case 1: div_dispatch<double, 1>(m, sa, ph, s); break;
+      case 2: div_dispatch<double, 2>(m, sa, ph, s); break;
+      default: div_dispatch<double, 4>(m, sa, ph, s); break;
     }
   } else {
     switch (lanes) {
-      case 4: div_dispatch<float, 4>(m, Us, Un, out, mode, a, b, dt_fixed, ph, s); break;
-      case 16: div_dispatch<float, 16>(m, Us, Un, out, mode, a, b, dt_fixed, ph, s); break;
-      default: div_dispatch<float, 8>(m, Us, Un, out, mode, a, b, dt_fixed, ph, s); break;
+      case 1: div_dispatch<float, 1>(m, sa, ph, s); break;
+      case 2: div_dispatch<float, 2>(m, sa, ph, s); break;
+      default: div_dispatch<float, 4>(m, sa, ph, s); break;
     }
   }
   return cudaGetLastError();
 }
 
+template <typename T, int G, bool VISC>
+static const void* stage_fn() {
+  return reinterpret_cast<const void*>(&k_stage<T, G, VISC>);
+}
+
+static const void* pick_stage_fn(const DevMesh& m, int lanes) {
+  if (m.precision == 0) {
+    if (m.viscous) return lanes == 1 ? stage_fn<double, 1, true>() : lanes == 2 ? stage_fn<double, 2, true>() : stage_fn<double, 4, true>();
+    return lanes == 1 ? stage_fn<double, 1, false>() : lanes == 2 ? stage_fn<double, 2, false>() : stage_fn<double, 4, false>();
+  }
+  if (m.viscous) return lanes == 1 ? stage_fn<float, 1, true>() : lanes == 2 ? stage_fn<float, 2, true>() : stage_fn<float, 4, true>();
+  return lanes == 1 ? stage_fn<float, 1, false>() : lanes == 2 ? stage_fn<float, 2, false>() : stage_fn<float, 4, false>();
+}
+
+cudaError_t persistent_max_blocks(const DevMesh& m, int lanes, int* per_sm, int* nsm) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pick_stage_fn(m, lanes), 128, 0);
+  return e;
+}
+
+cudaError_t launch_stage_persistent(const DevMesh& m, const double* Us, const double* Un,
+                                    double* out, int mode, double a, double b, double dt_fixed,
+                                    const Phys& ph, int lanes, int grid, bool do_ghost,
+                                    cudaStream_t s) {
+  KernelArgs ka = kernel_args(m);
+  StageArgs sa{Us, Un, out, mode, a, b, dt_fixed};
+  Phys p = ph;
+  int dg = do_ghost && m.G > 0 ? 1 : 0;
+  void* args[] = {&ka, &sa, &p, &dg};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(128);
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, pick_stage_fn(m, lanes), args);
+}
+
 cudaError_t launch_dtmin(const DevMesh& m, const double* U, const Phys& ph, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(m.dtbits, 0xff, sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(m.dtbits, 0xff, sizeof(unsigned long long) * m.nmember, s);
   if (e != cudaSuccess) return e;
   if (m.A == 0) return cudaSuccess;
-  k_dtmin<<<blocks(m.A, 256), 256, 0, s>>>(m.A, m.V, U, m.lmin, ph.gamma, m.dtbits);
+  int nb = blocks(m.A, 256);
+  k_dtmin<<<nb, 256, 0, s>>>(m.A, m.V, U, m.lmin, m.vmem, ph.gamma, m.dtbits, m.dtpartial);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_dtmin_final<<<1, 1024, 0, s>>>(nb, m.A, m.vmem, m.dtpartial, m.dtbits);
   return cudaGetLastError();
 }
 

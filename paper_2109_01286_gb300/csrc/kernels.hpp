@@ -37,9 +37,14 @@ struct DevMesh {
   int32_t *gid = nullptr, *gdonor = nullptr, *gflags = nullptr;
   // time step
   double* lmin = nullptr;                 // [A] shortest incident edge
-  unsigned long long* dtbits = nullptr;   // min over vertices of lmin/(|u|+c), as bits
-  double* dt_last = nullptr;
+  unsigned long long* dtbits = nullptr;   // [nmember] min over vertices of lmin/(|u|+c), as bits
+  double* dtpartial = nullptr;            // [ceil(A/256)] per-block minima of the dt reduction
+  double* dt_last = nullptr;              // [nmember] dt used by the last stage
   unsigned* err = nullptr;                // device error word
+  unsigned* bar = nullptr;                // grid barrier state of the persistent kernel [2]
+  unsigned barrier_spins = 1u << 24;      // poll bound of a grid barrier wait
+  int nmember = 1;                        // meshes in a batch (1 for a single mesh)
+  int32_t* vmem = nullptr;                // [A] mesh of each active vertex (batches only)
   // scratch: AoS copies of the state [V][12], vertex fluxes [V][8] (+ viscous), edge fluxes [Ef][4]
   void* Ua = nullptr;
   void* FG = nullptr;
@@ -48,6 +53,19 @@ struct DevMesh {
 };
 
 enum DivMode { DIV_RESIDUAL = 0, DIV_STAGE = 1 };
+
+// Everything the persistent stage kernel reads, passed by value.
+struct KernelArgs {
+  int V, A, Ef, G;
+  const int32_t *sten, *vptr, *vidx, *eptr, *eidx, *gid, *gdonor, *gflags, *vmem;
+  const void *nrm, *w5, *w3, *cv, *ce, *cvis;
+  void *Ua, *FG, *FGv, *h;
+  unsigned long long* dtbits;
+  double* dt_last;
+  unsigned* err;
+  unsigned* bar;
+  unsigned spins;
+};
 
 cudaError_t launch_ghost(const DevMesh& m, double* U, cudaStream_t s);
 cudaError_t launch_vertex(const DevMesh& m, const double* U, const Phys& ph, cudaStream_t s);
@@ -58,6 +76,13 @@ cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, dou
                        int mode, double a, double b, double dt_fixed, const Phys& ph,
                        int lanes, cudaStream_t s);
 cudaError_t launch_dtmin(const DevMesh& m, const double* U, const Phys& ph, cudaStream_t s);
+// One cooperative launch running ghost refresh (optional), vertex fluxes, edge fluxes and the
+// divergence + stage update of one RK stage, phases separated by bounded grid barriers.
+cudaError_t launch_stage_persistent(const DevMesh& m, const double* Us, const double* Un,
+                                    double* out, int mode, double a, double b, double dt_fixed,
+                                    const Phys& ph, int lanes, int grid, bool do_ghost,
+                                    cudaStream_t s);
+cudaError_t persistent_max_blocks(const DevMesh& m, int lanes, int* per_sm, int* nsm);
 cudaError_t launch_permute(int V, const int32_t* perm, const double* src, double* dst,
                            bool gather, cudaStream_t s);
 

@@ -17,7 +17,9 @@ struct hfd_mesh {
   hfd_options opts{};
   hfd::DevMesh dm;
   hfd::Phys ph{};
-  int lanes = 8;
+  int lanes = 4;                        // lanes per vertex in the divergence kernel (1, 2, 4)
+  int persistent = 0;                   // 1: one cooperative launch per RK stage
+  int grid = 0;                         // blocks of the persistent launch (0: all resident)
   std::vector<int32_t> perm;            // internal -> input
   int32_t* dperm = nullptr;             // device copy of perm
   double* U1 = nullptr;                 // stage buffers 12 x V
@@ -29,5 +31,11 @@ struct hfd_mesh {
   hfd_mesh_stats stats{};
   std::vector<void*> allocs;
   int device = 0;
+  // adjoint (built on the first hfd_adjoint call): transposed divergence / stencil lists,
+  // per-edge node sensitivities [Ef][72], two adjoint stage buffers 12 x V
+  int32_t *adj_tv_ptr = nullptr, *adj_tv_row = nullptr, *adj_tv_pos = nullptr;
+  int32_t *adj_te_ptr = nullptr, *adj_te_row = nullptr, *adj_te_pos = nullptr;
+  int32_t *adj_ts_ptr = nullptr, *adj_ts_ent = nullptr;
+  double *adj_Ge = nullptr, *adj_B1 = nullptr, *adj_B2 = nullptr;
 };
 

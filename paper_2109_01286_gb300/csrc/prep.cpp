@@ -841,6 +841,87 @@ Arr lookup(const Prep* P, const char* name) {
 }
 }  // namespace
 
+hfd_status hfd_prep_concat(const hfd_prep* const* preps, int32_t n, hfd_prep** out) {
+  if (!preps || n <= 0 || !out) { hfd::set_error("hfd_prep_concat: invalid argument"); return HFD_ERR_ARG; }
+  *out = nullptr;
+  const hfd_options& o0 = preps[0]->opts;
+  for (int k = 0; k < n; ++k) {
+    if (!preps[k]) { hfd::set_error("hfd_prep_concat: null prep %d", k); return HFD_ERR_ARG; }
+    const hfd_options& o = preps[k]->opts;
+    if (o.viscous != o0.viscous || o.gamma != o0.gamma || o.mu != o0.mu || o.prandtl != o0.prandtl ||
+        o.R_gas != o0.R_gas || o.weno_eps != o0.weno_eps || o.sens_lo != o0.sens_lo ||
+        o.sens_hi != o0.sens_hi || o.harten != o0.harten || o.cfl != o0.cfl ||
+        o.precision != o0.precision) {
+      hfd::set_error("hfd_prep_concat: member %d has different physical/numerical options", k);
+      return HFD_ERR_ARG;
+    }
+  }
+  hfd_prep* B = new (std::nothrow) hfd_prep();
+  if (!B) { hfd::set_error("hfd_prep_concat: out of host memory"); return HFD_ERR_ARG; }
+  B->opts = o0;
+  B->nmember = n;
+  int64_t voff = 0, eoff = 0;
+  for (int k = 0; k < n; ++k) {
+    const Prep& P = *preps[k];
+    const int32_t vo = (int32_t)voff, eo = (int32_t)eoff;
+    auto addv = [&](std::vector<int32_t>& dst, const std::vector<int32_t>& src, int32_t off) {
+      for (int32_t v : src) dst.push_back(v + off);
+    };
+    B->x.insert(B->x.end(), P.x.begin(), P.x.end());
+    B->y.insert(B->y.end(), P.y.begin(), P.y.end());
+    addv(B->tri, P.tri, vo);
+    addv(B->ghost_ids, P.ghost_ids, vo);
+    addv(B->ghost_donor, P.ghost_donor, vo);
+    B->ghost_flags.insert(B->ghost_flags.end(), P.ghost_flags.begin(), P.ghost_flags.end());
+    B->is_ghost.insert(B->is_ghost.end(), P.is_ghost.begin(), P.is_ghost.end());
+    addv(B->edges, P.edges, vo);
+    addv(B->active, P.active, vo);
+    const int64_t A0 = (int64_t)B->div_vptr.size() ? B->div_vptr.back() : 0;
+    const int64_t E0 = (int64_t)B->div_eptr.size() ? B->div_eptr.back() : 0;
+    const int64_t C0 = (int64_t)B->div_cptr.size() ? B->div_cptr.back() : 0;
+    const int64_t Z0 = (int64_t)B->visc_cptr.size() ? B->visc_cptr.back() : 0;
+    if (B->div_vptr.empty()) { B->div_vptr.push_back(0); B->div_eptr.push_back(0); B->div_cptr.push_back(0); }
+    if (P.opts.viscous && B->visc_cptr.empty()) B->visc_cptr.push_back(0);
+    for (size_t r = 1; r < P.div_vptr.size(); ++r) {
+      B->div_vptr.push_back((int32_t)(A0 + P.div_vptr[r]));
+      B->div_eptr.push_back((int32_t)(E0 + P.div_eptr[r]));
+      B->div_cptr.push_back(C0 + P.div_cptr[r]);
+      if (P.opts.viscous) B->visc_cptr.push_back(Z0 + P.visc_cptr[r]);
+    }
+    addv(B->div_vidx, P.div_vidx, vo);
+    addv(B->div_eidx, P.div_eidx, eo);
+    B->div_degree.insert(B->div_degree.end(), P.div_degree.begin(), P.div_degree.end());
+    B->div_coef.insert(B->div_coef.end(), P.div_coef.begin(), P.div_coef.end());
+    B->visc_coef.insert(B->visc_coef.end(), P.visc_coef.begin(), P.visc_coef.end());
+    addv(B->flux_edges, P.flux_edges, eo);
+    addv(B->stencil, P.stencil, vo);
+    B->normal.insert(B->normal.end(), P.normal.begin(), P.normal.end());
+    B->w5.insert(B->w5.end(), P.w5.begin(), P.w5.end());
+    B->w3.insert(B->w3.end(), P.w3.begin(), P.w3.end());
+    B->rank.insert(B->rank.end(), P.rank.begin(), P.rank.end());
+    B->lmin.insert(B->lmin.end(), P.lmin.begin(), P.lmin.end());
+    B->member.insert(B->member.end(), (size_t)P.nv, k);
+    // the member's own space-filling-curve box, as a single mesh would use it
+    double x0 = 0, x1 = P.Lx, y0 = 0, y1 = P.Ly;
+    if (!P.periodic_x || !(x1 > 0)) {
+      x0 = *std::min_element(P.x.begin(), P.x.end());
+      x1 = *std::max_element(P.x.begin(), P.x.end());
+    }
+    if (!P.periodic_y || !(y1 > 0)) {
+      y0 = *std::min_element(P.y.begin(), P.y.end());
+      y1 = *std::max_element(P.y.begin(), P.y.end());
+    }
+    B->member_box.insert(B->member_box.end(), {x0, x1, y0, y1});
+    B->degree_fallbacks += P.degree_fallbacks;
+    B->prep_seconds += P.prep_seconds;
+    voff += P.nv;
+    eoff += P.nedges();
+  }
+  B->nv = (int32_t)voff;
+  *out = B;
+  return HFD_OK;
+}
+
 int64_t hfd_prep_size(const hfd_prep* p, const char* name) {
   if (!p) return -1;
   return lookup(p, name).n;

@@ -39,6 +39,11 @@ struct Prep {
   std::vector<double> w3;                      // 18*Ef: side, sub-stencil, node
   std::vector<int32_t> rank;                   // 2*Ef
   std::vector<double> lmin;                    // nv: shortest incident edge (time step)
+  // batches (hfd_prep_concat): member mesh of each vertex and each member's bounding box
+  // (x0, x1, y0, y1) for the space-filling-curve keys; empty / 1 for a single mesh
+  std::vector<int32_t> member;
+  int32_t nmember = 1;
+  std::vector<double> member_box;
   int64_t degree_fallbacks = 0;
   double prep_seconds = 0;
 

@@ -26,7 +26,9 @@ EXPORTED = ["hfd_default_options", "hfd_last_error", "hfd_prep_create", "hfd_pre
             "hfd_prep_size", "hfd_prep_get", "hfd_prep_set", "hfd_mesh_create", "hfd_mesh_upload",
             "hfd_mesh_destroy", "hfd_mesh_info", "hfd_mesh_perm", "hfd_state_import",
             "hfd_state_export", "hfd_residual", "hfd_step", "hfd_steps", "hfd_steps_host",
-            "hfd_last_dt", "hfd_check", "hfd_steps_profiled", "hfd_residual_static"]
+            "hfd_last_dt", "hfd_check", "hfd_steps_profiled", "hfd_residual_static",
+            "hfd_prep_concat", "hfd_mesh_set_launch", "hfd_mesh_autotune",
+            "hfd_mesh_set_barrier_limit", "hfd_adjoint"]
 
 
 class HfdError(RuntimeError):
@@ -64,7 +66,8 @@ class MeshStats(ctypes.Structure):
                 ("div_nv_total", ctypes.c_int64), ("div_ne_total", ctypes.c_int64),
                 ("div_nv_max", ctypes.c_int32), ("div_ne_max", ctypes.c_int32),
                 ("rank_hist", ctypes.c_int64 * 16), ("div_degree_fallbacks", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("prep_seconds", ctypes.c_double)]
+                ("device_bytes", ctypes.c_int64), ("prep_seconds", ctypes.c_double),
+                ("nmember", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -87,10 +90,15 @@ _lib.hfd_state_import.argtypes = [_P, _P, _P, _P]
 _lib.hfd_state_export.argtypes = [_P, _P, _P, _P]
 _lib.hfd_residual.argtypes = [_P, _P, _P, _P]
 _lib.hfd_residual_static.argtypes = [_P, _P, _P, _P]
+_lib.hfd_prep_concat.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_P)]
+_lib.hfd_mesh_set_launch.argtypes = [_P, ctypes.c_int32, ctypes.c_int32]
+_lib.hfd_mesh_autotune.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int32)]
+_lib.hfd_mesh_set_barrier_limit.argtypes = [_P, ctypes.c_uint32]
+_lib.hfd_adjoint.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
 _lib.hfd_step.argtypes = [_P, _P, ctypes.c_double, _P]
 _lib.hfd_steps.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int32, _P]
 _lib.hfd_steps_host.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_int32, _P]
-_lib.hfd_last_dt.argtypes = [_P, ctypes.POINTER(ctypes.c_double), _P]
+_lib.hfd_last_dt.argtypes = [_P, _P, _P]
 _lib.hfd_check.argtypes = [_P, _P]
 
 
@@ -148,12 +156,25 @@ class Prep:
     """Host-only geometric preprocessing (hfd_prep_*): needs no GPU."""
 
     def __init__(self, mesh, **opts):
+        if mesh is None:                      # filled by concat()
+            self._h = None
+            return
         self.options = options(**opts)
         d, keep = _desc(mesh)
         h = _P()
         _ok(_lib.hfd_prep_create(ctypes.byref(d), ctypes.byref(self.options), ctypes.byref(h)),
             "hfd_prep_create")
         self._h = h
+
+    @classmethod
+    def concat(cls, preps):
+        """Batch: the disjoint union of several preps (hfd_prep_concat)."""
+        arr = (_P * len(preps))(*[p._h for p in preps])
+        h = _P()
+        _ok(_lib.hfd_prep_concat(arr, len(preps), ctypes.byref(h)), "hfd_prep_concat")
+        out = cls(None)
+        out._h = h
+        return out
 
     def get(self, name):
         n = _lib.hfd_prep_size(self._h, name.encode())
@@ -271,16 +292,40 @@ class Mesh:
     def steps_profiled(self, U, dt, n, stream=None):
         """Like steps() but kernel by kernel with CUDA events; returns (ms per kernel kind
         {ghost, vertex, edge, div, dt}, number of launches).  Synchronises."""
-        ms = (ctypes.c_double * 5)()
+        ms = (ctypes.c_double * 6)()
         nl = ctypes.c_int64()
         _ok(_lib.hfd_steps_profiled(self._h, _dptr(U), float(dt), int(n), _stream(stream), ms,
                                     ctypes.byref(nl)), "hfd_steps_profiled")
-        return dict(zip(["ghost", "vertex", "edge", "div", "dt"], list(ms))), int(nl.value)
+        return (dict(zip(["ghost", "vertex", "edge", "div", "dt", "stage"], list(ms))),
+                int(nl.value))
+
+    def adjoint(self, U_n, lam_np1, lam_n=None, dt=None, stream=None):
+        """lam_n = (d step(U_n, dt) / d U_n)^T lam_np1 (hfd_adjoint; fixed dt > 0)."""
+        import torch
+        lam_n = torch.empty_like(lam_np1) if lam_n is None else lam_n
+        _ok(_lib.hfd_adjoint(self._h, _dptr(U_n), _dptr(lam_np1), _dptr(lam_n), float(dt),
+                             _stream(stream)), "hfd_adjoint")
+        return lam_n
+
+    def set_launch(self, persistent, grid=0):
+        _ok(_lib.hfd_mesh_set_launch(self._h, int(bool(persistent)), int(grid)),
+            "hfd_mesh_set_launch")
+
+    def set_barrier_limit(self, polls):
+        _ok(_lib.hfd_mesh_set_barrier_limit(self._h, int(polls)), "hfd_mesh_set_barrier_limit")
+
+    def autotune(self, U, stream=None):
+        """Pick the fastest launch shape for one RK stage on state U; returns (persistent, grid)."""
+        c = (ctypes.c_int32 * 2)()
+        _ok(_lib.hfd_mesh_autotune(self._h, _dptr(U), _stream(stream), c), "hfd_mesh_autotune")
+        return int(c[0]), int(c[1])
 
     def last_dt(self, stream=None):
-        v = ctypes.c_double()
-        _ok(_lib.hfd_last_dt(self._h, ctypes.byref(v), _stream(stream)), "hfd_last_dt")
-        return v.value
+        """dt of the last step: a float, or one value per member for a batch."""
+        n = max(1, int(self.stats.nmember))
+        v = (ctypes.c_double * n)()
+        _ok(_lib.hfd_last_dt(self._h, v, _stream(stream)), "hfd_last_dt")
+        return v[0] if n == 1 else list(v)
 
     def check(self, stream=None):
         _ok(_lib.hfd_check(self._h, _stream(stream)), "hfd_check")

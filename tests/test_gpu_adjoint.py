@@ -1,0 +1,72 @@
+"""GPU tests of the discrete adjoint (hfd_adjoint) and its torch.autograd wrapper."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import adjoint as ADJ
+from gpu_helpers import inject_oracle_coefficients
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2109_01286_gb300 as pkg
+    return pkg
+
+
+def test_adjoint_step_matches_oracle_adjoint_20x20():
+    """The GPU adjoint of one step against the oracle's adjoint on a 20 x 20 vortex mesh, with
+    the oracle's coefficients in both (kernel parity)."""
+    pkg = _pkg()
+    m = synth.jittered_grid(20, 20, 10.0, 10.0, seed=5)
+    U = synth.isentropic_vortex(m)
+    P = oracle.prepare(m)
+    dt = oracle.cfl_dt(m, P, U)
+    lam = np.random.default_rng(0).standard_normal(U.shape)
+    ref = ADJ.step_vjp(m, P, U, dt, lam)
+    prep = pkg.Prep(m)
+    inject_oracle_coefficients(prep, P, len(m["x"]))
+    mesh = prep.upload()
+    Ui = mesh.import_state(torch.from_numpy(U).cuda())
+    li = mesh.import_state(torch.from_numpy(lam).cuda())
+    out = mesh.export_state(mesh.adjoint(Ui, li, dt=dt)).cpu().numpy()
+    err = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    assert err < 1e-11, err
+
+
+def test_adjoint_rollout_against_central_differences():
+    """<grad, delta> from the autograd rollout (checkpointed adjoint) against central finite
+    differences of the objective sum_v A_v (rho - rho_ref)^2 (step 1e-6)."""
+    pkg = _pkg()
+    m = synth.jittered_grid(32, 32, 10.0, 10.0, seed=6)
+    U0 = synth.isentropic_vortex(m)
+    mesh = pkg.Mesh(m)
+    dt = 0.03
+    area = torch.from_numpy(oracle.vertex_areas(m)).cuda()
+    rho_ref = torch.from_numpy(synth.isentropic_vortex(m, t=10 * dt)[0]).cuda()
+    perm = torch.from_numpy(mesh.perm.astype(np.int64)).cuda()
+    area_i, rho_ref_i = area[perm], rho_ref[perm]
+
+    def J(Ui):
+        UN = pkg.autograd.rollout(Ui, mesh, dt, 10, every=4)
+        return torch.sum(area_i * (UN[0] - rho_ref_i) ** 2)
+
+    U0i = mesh.import_state(torch.from_numpy(U0).cuda()).requires_grad_(True)
+    val = J(U0i)
+    val.backward()
+    g = U0i.grad.detach()
+    rng = np.random.default_rng(7)
+    for _ in range(4):
+        d = torch.from_numpy(rng.standard_normal(U0.shape)).cuda()
+        d = mesh.import_state(d)
+        eps = 1e-6
+        with torch.no_grad():
+            jp = J((U0i + eps * d).detach()).item()
+            jm = J((U0i - eps * d).detach()).item()
+        fd = (jp - jm) / (2 * eps)
+        ad = torch.sum(g * d).item()
+        assert abs(fd - ad) <= 1e-5 * max(abs(fd), 1e-12), (fd, ad)

@@ -1,0 +1,112 @@
+"""GPU tests of batches (many meshes advanced together) and of the persistent launch."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2109_01286_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def members():
+    return synth.batched_vortices(n=3, seed=11, vmin=300, vmax=1500)
+
+
+def _state(mesh, U):
+    return mesh.import_state(torch.from_numpy(np.ascontiguousarray(U)).cuda())
+
+
+def test_batch_residual_and_steps_equal_single_meshes(members):
+    pkg = _pkg()
+    preps = [pkg.Prep(x["mesh"]) for x in members]
+    batch = pkg.Prep.concat(preps).upload()
+    assert batch.stats.nmember == 3
+    Ub = np.concatenate([x["U"] for x in members], axis=1)
+    Rb = batch.export_state(batch.residual(_state(batch, Ub))).cpu().numpy()
+    Xb = _state(batch, Ub)
+    batch.steps(Xb, 0.0, 2)                                    # own CFL step per member
+    Sb = batch.export_state(Xb).cpu().numpy()
+    dts = batch.last_dt()
+    off = 0
+    for k, x in enumerate(members):
+        single = preps[k].upload()
+        V = x["U"].shape[1]
+        R = single.export_state(single.residual(_state(single, x["U"]))).cpu().numpy()
+        np.testing.assert_array_equal(Rb[:, off:off + V], R)
+        X = _state(single, x["U"])
+        single.steps(X, 0.0, 2)
+        np.testing.assert_array_equal(Sb[:, off:off + V], single.export_state(X).cpu().numpy())
+        assert dts[k] == single.last_dt()
+        off += V
+    assert len(set(dts)) == 3
+
+
+def test_batch_matches_oracle_residual(members):
+    pkg = _pkg()
+    x = members[0]
+    P = oracle.prepare(x["mesh"])
+    R_ref = oracle.residual(x["mesh"], P, x["U"].copy())
+    batch = pkg.Prep.concat([pkg.Prep(y["mesh"]) for y in members]).upload()
+    Ub = np.concatenate([y["U"] for y in members], axis=1)
+    Rb = batch.export_state(batch.residual(_state(batch, Ub))).cpu().numpy()
+    V = x["U"].shape[1]
+    err = np.linalg.norm(Rb[:, :V] - R_ref) / np.linalg.norm(R_ref)
+    assert err < 1e-7, err                    # full path (library coefficients), see parity tests
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_persistent_launch_equals_four_launch_stage(members, precision):
+    """The persistent stage kernel runs the same per-entity code as the four separate kernels;
+    the compiler may contract multiply-adds differently in the fused kernel, so the results
+    agree to rounding of the path's precision."""
+    pkg = _pkg()
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    batch = pkg.Prep.concat([pkg.Prep(y["mesh"]) for y in members]).upload(precision)
+    Ub = np.concatenate([y["U"] for y in members], axis=1)
+    a = _state(batch, Ub)
+    b = a.clone()
+    batch.set_launch(False)
+    batch.steps(a, 0.0, 2)
+    batch.set_launch(True)
+    batch.steps(b, 0.0, 2)
+    torch.cuda.synchronize()
+    batch.check()
+    assert (torch.linalg.norm(a - b) / torch.linalg.norm(a)).item() < tol
+    persistent, grid = batch.autotune(_state(batch, Ub))
+    assert persistent in (0, 1)
+    c = _state(batch, Ub)
+    batch.steps(c, 0.0, 2)
+    torch.cuda.synchronize()
+    assert (torch.linalg.norm(a - c) / torch.linalg.norm(a)).item() < tol
+
+
+def test_persistent_barrier_wait_gives_up_and_reports_timeout(members):
+    """A barrier poll bound of zero makes every early-arriving block give up at once: the kernel
+    ends, the error word says HFD_ERR_TIMEOUT, and the mesh works again afterwards."""
+    pkg = _pkg()
+    m = pkg.Prep(members[2]["mesh"]).upload()
+    U = _state(m, members[2]["U"])
+    m.set_launch(True, 0)
+    m.set_barrier_limit(0)
+    m.step(U.clone(), 0.01)
+    with pytest.raises(pkg.HfdError) as e:
+        m.check()
+    assert e.value.status == 8
+    m.set_barrier_limit(1 << 24)
+    a = U.clone()
+    m.step(a, 0.01)
+    m.check()
+    m.set_launch(False)
+    b = U.clone()
+    m.step(b, 0.01)
+    torch.cuda.synchronize()
+    assert (torch.linalg.norm(a - b) / torch.linalg.norm(a)).item() < 1e-12

@@ -265,3 +265,27 @@ def test_full_size_four_quadrant_sampled_vertices():
         for g, rows in enumerate((slice(0, 4), slice(4, 12))):
             diff = np.linalg.norm(R[rows, v] - R_ref[rows, v])
             assert diff < TOL_FP64 * np.linalg.norm(R_ref[rows, v]) + floors[g], (v, g, diff)
+
+
+def test_vortex_trajectory_parity_20_steps(c1):
+    """The 40 x 40 isentropic-vortex workload: 20 SSP-RK3 steps at CFL 0.3 (device time step)
+    against the oracle's 20 steps (its own CFL step each time), with the oracle's coefficients
+    (kernel parity); also the density error against the exact translated vortex."""
+    pkg = _hfd()
+    m, P, U = c1
+    mesh = _kernel_mesh(pkg, m, P)
+    X = mesh.import_state(torch.from_numpy(U).cuda())
+    ref = U.copy()
+    t = 0.0
+    for _ in range(20):
+        dt = oracle.cfl_dt(m, P, ref)
+        ref = oracle.step(m, P, ref, dt)
+        mesh.step(X, 0.0)
+        assert abs(mesh.last_dt() - dt) <= 1e-12 * dt
+        t += dt
+    out = mesh.export_state(X).cpu().numpy()
+    err = rel_l2_groups(out, ref)
+    assert max(err) < 1e-10, err
+    exact = synth.isentropic_vortex(m, t=t)
+    l2 = np.sqrt(np.mean((out[0] - exact[0]) ** 2))
+    assert l2 < 5e-3, l2
