@@ -254,9 +254,9 @@ hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
   // lanes per vertex in the divergence: FP64 is bound by the FP64 pipe and runs best without a
   // cross-lane reduction (1); the FP32 path is bound by memory and prefers coalesced groups (4)
   m->lanes = m->opts.precision == 0 ? 1 : 4;
-  if (const char* env = getenv("HFD_DIV_LANES")) {   // tuning override: 1, 2 or 4
+  if (const char* env = getenv("HFD_DIV_LANES")) {   // tuning override: 1, 2, 4 or 8
     int l = atoi(env);
-    if (l == 1 || l == 2 || l == 4) m->lanes = l;
+    if (l == 1 || l == 2 || l == 4 || l == 8) m->lanes = l;
   }
   const hfd_options& o = P.opts;
   m->ph.gamma = o.gamma;

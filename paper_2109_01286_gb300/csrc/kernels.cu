@@ -401,8 +401,15 @@ __device__ __forceinline__ void edge_body(int e, int Ef, const int32_t* __restri
   st4(h + (size_t)e * 4, hq);
 }
 
+// Resident blocks of 128 threads the compiler must allow: 3 for FP64 data (<= 170 registers; an
+// explicit bound of 1 lets it take ~214 and lose a block), 4 for FP32 data (5 would spill).
 template <typename T>
-__global__ void __launch_bounds__(128) k_edge(int Ef, const int32_t* __restrict__ sten,
+struct EdgeOcc { static constexpr int kMinBlocks = 3; };
+template <>
+struct EdgeOcc<float> { static constexpr int kMinBlocks = 4; };
+
+template <typename T>
+__global__ void __launch_bounds__(128, EdgeOcc<T>::kMinBlocks) k_edge(int Ef, const int32_t* __restrict__ sten,
                                               const T* __restrict__ nrm, const T* __restrict__ w5,
                                               const T* __restrict__ w3, const T* __restrict__ Ua,
                                               T* __restrict__ h, Phys ph) {
@@ -428,12 +435,26 @@ __device__ __forceinline__ void reduce_scatter12(T* acc, int lane) {
     }
   }
   if (G >= 4) {
-    bool hi = (lane & 1) != 0;
+    const int o = G / 4;
+    bool hi = (lane & o) != 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       T keep = hi ? acc[3 + i] : acc[i];
       T send = hi ? acc[i] : acc[3 + i];
-      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1, G);
+      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o, G);
+    }
+  }
+  if (G >= 8) {
+    // three values left: the lane with bit 0 clear keeps rows 0-1, its partner keeps row 2
+    bool hi = (lane & 1) != 0;
+    T r0 = __shfl_xor_sync(0xffffffffu, acc[0], 1, G);
+    T r1 = __shfl_xor_sync(0xffffffffu, acc[1], 1, G);
+    T r2 = __shfl_xor_sync(0xffffffffu, acc[2], 1, G);
+    if (hi) {
+      acc[0] = acc[2] + r2;
+    } else {
+      acc[0] += r0;
+      acc[1] += r1;
     }
   }
 }
@@ -472,10 +493,9 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
     int n0 = __ldg(vptr + r), N = __ldg(vptr + r + 1) - n0;
     const T* c = cv + 6 * (size_t)n0;
     const T* cz = VISC ? cvis + 6 * (size_t)n0 : nullptr;
-    for (int j = lane; j < N; j += G) {
-      int uu = __ldg(vidx + n0 + j);
-      T f[8];
-      ld8(FG + (size_t)uu * 8, f);
+    // vertex entries, two per lane per iteration so that both entries' loads are in flight
+    // before their multiply-adds (the same per-lane summation order as one at a time)
+    auto vtx = [&](int j, const T* f, const T* fv) {
       T c0f = __ldg(c + j), c0g = __ldg(c + N + j), cxf = __ldg(c + 2 * N + j);
       T cxg = __ldg(c + 3 * N + j), cyf = __ldg(c + 4 * N + j), cyg = __ldg(c + 5 * N + j);
 #pragma unroll
@@ -485,30 +505,61 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
         acc[8 + q] = fma(cyg, f[4 + q], fma(cyf, f[q], acc[8 + q]));
       }
       if (VISC) {
-        ld8(FGv + (size_t)uu * 8, f);
         c0f = __ldg(cz + j); c0g = __ldg(cz + N + j); cxf = __ldg(cz + 2 * N + j);
         cxg = __ldg(cz + 3 * N + j); cyf = __ldg(cz + 4 * N + j); cyg = __ldg(cz + 5 * N + j);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          acc[q] = fma(-c0g, f[4 + q], fma(-c0f, f[q], acc[q]));
-          acc[4 + q] = fma(-cxg, f[4 + q], fma(-cxf, f[q], acc[4 + q]));
-          acc[8 + q] = fma(-cyg, f[4 + q], fma(-cyf, f[q], acc[8 + q]));
+          acc[q] = fma(-c0g, fv[4 + q], fma(-c0f, fv[q], acc[q]));
+          acc[4 + q] = fma(-cxg, fv[4 + q], fma(-cxf, fv[q], acc[4 + q]));
+          acc[8 + q] = fma(-cyg, fv[4 + q], fma(-cyf, fv[q], acc[8 + q]));
         }
       }
+    };
+    int j = lane;
+    for (; j + G < N; j += 2 * G) {
+      int u0 = __ldg(vidx + n0 + j), u1 = __ldg(vidx + n0 + j + G);
+      T f0[8], f1[8], g0[8], g1[8];
+      ld8(FG + (size_t)u0 * 8, f0);
+      ld8(FG + (size_t)u1 * 8, f1);
+      if (VISC) {
+        ld8(FGv + (size_t)u0 * 8, g0);
+        ld8(FGv + (size_t)u1 * 8, g1);
+      }
+      vtx(j, f0, g0);
+      vtx(j + G, f1, g1);
+    }
+    if (j < N) {
+      int u0 = __ldg(vidx + n0 + j);
+      T f0[8], g0[8];
+      ld8(FG + (size_t)u0 * 8, f0);
+      if (VISC) ld8(FGv + (size_t)u0 * 8, g0);
+      vtx(j, f0, g0);
     }
     int m0 = __ldg(eptr + r), M = __ldg(eptr + r + 1) - m0;
     const T* d = ce + 3 * (size_t)m0;
-    for (int j = lane; j < M; j += G) {
-      int e = __ldg(eidx + m0 + j);
-      T hv[4];
-      ld4(h + (size_t)e * 4, hv);
-      T d0 = __ldg(d + j), dx = __ldg(d + M + j), dy = __ldg(d + 2 * M + j);
+    auto edg = [&](int jj, const T* hv) {
+      T d0 = __ldg(d + jj), dx = __ldg(d + M + jj), dy = __ldg(d + 2 * M + jj);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         acc[q] = fma(d0, hv[q], acc[q]);
         acc[4 + q] = fma(dx, hv[q], acc[4 + q]);
         acc[8 + q] = fma(dy, hv[q], acc[8 + q]);
       }
+    };
+    j = lane;
+    for (; j + G < M; j += 2 * G) {
+      int e0 = __ldg(eidx + m0 + j), e1 = __ldg(eidx + m0 + j + G);
+      T h0[4], h1[4];
+      ld4(h + (size_t)e0 * 4, h0);
+      ld4(h + (size_t)e1 * 4, h1);
+      edg(j, h0);
+      edg(j + G, h1);
+    }
+    if (j < M) {
+      int e0 = __ldg(eidx + m0 + j);
+      T h0[4];
+      ld4(h + (size_t)e0 * 4, h0);
+      edg(j, h0);
     }
   }
   reduce_scatter12<G>(acc, lane);
@@ -518,11 +569,16 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
   double dt = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)dtbits[mem]);
   if (mode == DIV_STAGE && lane == 0 && dt_last && (r == 0 || (vmem && __ldg(vmem + r - 1) != mem)))
     dt_last[mem] = dt;
-  const int per = 12 / G;
-  const int base = (G >= 2 && (lane & (G / 2)) ? 6 : 0) + (G >= 4 && (lane & 1) ? 3 : 0);
+  // rows held by this lane after the reduce-scatter: base .. base + per - 1
+  int per = G == 1 ? 12 : G == 2 ? 6 : 3;
+  int base = (G >= 2 && (lane & (G / 2)) ? 6 : 0) + (G >= 4 && (lane & (G / 4)) ? 3 : 0);
+  if (G >= 8) {
+    if (lane & 1) { base += 2; per = 1; } else { per = 2; }
+  }
   unsigned bad = 0;
 #pragma unroll
-  for (int i = 0; i < per; ++i) {
+  for (int i = 0; i < 12 / (G >= 8 ? 4 : G); ++i) {
+    if (i >= per) break;
     int k = base + i;
     double R = -(double)acc[i];
     size_t idx = (size_t)k * V + r;
@@ -541,9 +597,10 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
 }
 
 // FP32 data: memory-latency bound, so at least 4 resident blocks of 256 threads per SM; FP64
-// data: FP64-pipe bound, no occupancy constraint.
+// data: FP64-pipe bound, 2 blocks (without a bound the compiler takes ~168 registers and the
+// kernel loses half its warps).
 template <typename T>
-struct DivOcc { static constexpr int kMinBlocks = 1; };
+struct DivOcc { static constexpr int kMinBlocks = 2; };
 template <>
 struct DivOcc<float> { static constexpr int kMinBlocks = 4; };
 
@@ -814,12 +871,14 @@ cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, dou
     switch (lanes) {
       case 1: div_dispatch<double, 1>(m, sa, ph, s); break;
       case 2: div_dispatch<double, 2>(m, sa, ph, s); break;
+      case 8: div_dispatch<double, 8>(m, sa, ph, s); break;
       default: div_dispatch<double, 4>(m, sa, ph, s); break;
     }
   } else {
     switch (lanes) {
       case 1: div_dispatch<float, 1>(m, sa, ph, s); break;
       case 2: div_dispatch<float, 2>(m, sa, ph, s); break;
+      case 8: div_dispatch<float, 8>(m, sa, ph, s); break;
       default: div_dispatch<float, 4>(m, sa, ph, s); break;
     }
   }

@@ -289,3 +289,43 @@ def test_vortex_trajectory_parity_20_steps(c1):
     exact = synth.isentropic_vortex(m, t=t)
     l2 = np.sqrt(np.mean((out[0] - exact[0]) ** 2))
     assert l2 < 5e-3, l2
+
+
+@pytest.mark.parametrize("precision,lanes,tol", [("fp64", "2", 1e-13), ("fp64", "8", 1e-13),
+                                                 ("fp32", "1", 1e-4), ("fp32", "8", 1e-4)])
+def test_divergence_lane_counts_agree(c1, precision, lanes, tol, monkeypatch):
+    """Every lanes-per-vertex variant of the divergence (different reduction orders) gives the
+    default variant's residual to rounding."""
+    pkg = _hfd()
+    m, P, U = c1
+    prep = pkg.Prep(m)
+    R0 = _residual(prep.upload(precision), U)
+    monkeypatch.setenv("HFD_DIV_LANES", lanes)
+    R1 = _residual(prep.upload(precision), U)
+    assert np.linalg.norm(R1 - R0) <= tol * np.linalg.norm(R0)
+
+
+def test_viscous_steps_parity_taylor_green():
+    """Three SSP-RK3 steps of the viscous Taylor-Green workload (24 x 24 periodic, Mach 0.1,
+    mu 0.01) with a fixed step, through the graph-replayed stage path, against the oracle's
+    three steps (kernel parity)."""
+    pkg = _hfd()
+    n = 24
+    m = synth.jittered_grid(n, n, 2 * np.pi, 2 * np.pi, seed=3)
+    mach = 0.1
+    p0 = 1.0 / (1.4 * mach * mach)
+    kw = dict(viscous=True, mu=0.01, R_gas=p0)
+    opts = oracle.Options(**kw)
+    P = oracle.prepare(m, opts)
+    U = synth.taylor_green(m, mach=mach)
+    h = 2 * np.pi / n
+    dt = 0.3 * h / (1.0 + np.sqrt(1.4 * p0))
+    mesh = _kernel_mesh(pkg, m, P, **kw)
+    X = mesh.import_state(torch.from_numpy(U).cuda())
+    ref = U.copy()
+    for _ in range(3):
+        ref = oracle.step(m, P, ref, dt, opts)
+        mesh.steps(X, dt, 1)
+    out = mesh.export_state(X).cpu().numpy()
+    err = rel_l2_groups(out, ref)
+    assert max(err) < 1e-11, err
