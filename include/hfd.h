@@ -82,6 +82,9 @@ typedef struct {
   double div_cond_min;     /* LS degree drops by one below this sigma ratio estimate  [1e-12] */
   double harten;           /* entropy-fix width as a fraction of the Roe sound speed    [0.1] */
   double cfl;              /* CFL number of the device time step                        [0.3] */
+  double visc_coef_max;    /* viscous vertex-only LS: the degree drops by one (down to 2)
+                              while a first- or second-derivative weight, in coordinates
+                              scaled by the mean incident edge length, exceeds this       [8] */
 } hfd_options;
 
 typedef struct {
@@ -98,6 +101,7 @@ typedef struct {
   int64_t device_bytes;    /* device memory held by the mesh                                */
   double prep_seconds;     /* host preprocessing wall time                                  */
   int32_t nmember;         /* meshes in a batch (hfd_prep_concat), 1 otherwise              */
+  int64_t visc_degree_fallbacks; /* viscous rows whose degree dropped (visc_coef_max)       */
 } hfd_mesh_stats;
 
 typedef struct hfd_prep hfd_prep;

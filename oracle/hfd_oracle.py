@@ -42,6 +42,7 @@ class Options:
     visc_degree: int = 4          # R6: viscous LS degree ("fourth order")
     sv_rtol: float = 1e-13        # R3: singular values below rtol*sigma_max count as zero
     div_cond_min: float = 1e-12   # R6: fall back to degree-1 below this sigma_min/sigma_max
+    visc_coef_max: float = 8.0    # R6b: viscous LS degree drops while a scaled weight exceeds this
     harten: float = 0.1           # R9: entropy-fix width delta = harten * c_roe
     viscous: bool = False
     mu: float = 0.0
@@ -310,19 +311,28 @@ def div_rows(mesh, topo, v, opts):
 def visc_rows(mesh, topo, v, opts):
     """Vertex-only least-squares divergence rows of the viscous flux (Sec. 2.3, "Computing
     Viscous Flux"): f_vis and g_vis are fitted separately on the two-level vertex set with the
-    degree-opts.visc_degree Taylor basis.  Rows over the interleaved data [f_1, g_1, ...]:
-    e_0 (divergence), e_x, e_y (divergence of the x/y derivative fluxes)."""
+    Taylor basis of degree opts.visc_degree, in coordinates scaled by l_v.  Rows over the
+    interleaved data [f_1, g_1, ...]: e_0 (divergence), e_x, e_y (divergence of the x/y
+    derivative fluxes).  With only about as many stencil vertices as basis terms some vertex
+    sets are nearly unisolvent and the fitted weights explode; the degree then drops by one
+    while any scaled weight of the rows used (first and second derivatives) exceeds
+    opts.visc_coef_max (R6b), down to degree 2."""
     verts, _ = vertex_stencil(topo, v)
     ell = _vertex_scale(mesh, topo, v)
     xv = np.array([disp(mesh, v, u) for u in verts]) / ell
-    B = taylor_basis(xv[:, 0], xv[:, 1], opts.visc_degree)[0].T
-    Q = np.linalg.pinv(B)
+    deg = opts.visc_degree
+    while True:
+        B = taylor_basis(xv[:, 0], xv[:, 1], deg)[0].T
+        Q = np.linalg.pinv(B)
+        if np.abs(Q[1:6]).max() <= opts.visc_coef_max or deg <= 2:
+            break
+        deg -= 1
     N = len(verts)
     rows = np.zeros((3, 2 * N))
     rows[0, 0::2], rows[0, 1::2] = Q[1] / ell, Q[2] / ell
     rows[1, 0::2], rows[1, 1::2] = Q[3] / ell ** 2, Q[4] / ell ** 2
     rows[2, 0::2], rows[2, 1::2] = Q[4] / ell ** 2, Q[5] / ell ** 2
-    return verts, rows
+    return verts, rows, deg
 
 
 class Prep:
@@ -341,7 +351,7 @@ def prepare(mesh, opts=None, active=None, topo=None):
     active = np.asarray(active, dtype=np.int64)
     rows, cols, vals = [[], [], []], [[], [], []], [[], [], []]
     need = set()
-    degs = []
+    degs, vdegs = [], []
     vrows, vcols, vvals = [[], [], []], [[], [], []], [[], [], []]
     for r, v in enumerate(active):
         verts, edges, d, deg = div_rows(mesh, topo, int(v), opts)
@@ -353,7 +363,8 @@ def prepare(mesh, opts=None, active=None, topo=None):
             cols[k].append(col)
             vals[k].append(d[k])
         if opts.viscous:
-            vv, vr = visc_rows(mesh, topo, int(v), opts)
+            vv, vr, vdeg = visc_rows(mesh, topo, int(v), opts)
+            vdegs.append(vdeg)
             vcol = np.stack([2 * vv, 2 * vv + 1], 1).ravel()
             for k in range(3):
                 vrows[k].append(np.full(len(vcol), r))
@@ -362,6 +373,7 @@ def prepare(mesh, opts=None, active=None, topo=None):
     P = Prep()
     P.topo, P.active, P.opts = topo, active, opts
     P.div_degree = np.array(degs)
+    P.visc_degree = np.array(vdegs, dtype=np.int64)
     shape = (len(active), 2 * V + E)
     P.D = [sp.csr_matrix((np.concatenate(vals[k]), (np.concatenate(rows[k]),
                                                      np.concatenate(cols[k]))), shape=shape)

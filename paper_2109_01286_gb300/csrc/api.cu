@@ -282,6 +282,7 @@ hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
   }
   for (int32_t r : P.rank) s.rank_hist[std::min(15, std::max(0, r))]++;
   s.div_degree_fallbacks = P.degree_fallbacks;
+  s.visc_degree_fallbacks = P.visc_fallbacks;
   s.nmember = P.nmember;
   s.prep_seconds = P.prep_seconds;
   return HFD_OK;

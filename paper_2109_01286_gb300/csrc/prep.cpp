@@ -403,7 +403,7 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
     return HFD_ERR_ARG;
   }
   if (o->div_degree < 2 || o->div_degree > 6 || o->visc_degree < 2 || o->visc_degree > 6 ||
-      o->precision < 0 || o->precision > 1) {
+      o->precision < 0 || o->precision > 1 || !(o->visc_coef_max > 0.0)) {
     set_error("hfd_prep_create: option out of range");
     return HFD_ERR_ARG;
   }
@@ -575,9 +575,10 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
     P->visc_cptr.assign(A + 1, 0);
     for (int64_t r = 0; r < A; ++r) P->visc_cptr[r + 1] = P->visc_cptr[r] + 6 * (int64_t)sv[r].size();
     P->visc_coef.assign(P->visc_cptr[A], 0.0);
+    P->visc_degree.assign(A, 0);
   }
   ErrorSlot err;
-  std::atomic<int64_t> fallbacks(0);
+  std::atomic<int64_t> fallbacks(0), visc_fallbacks(0);
   parallel_for(A, nthreads, [&](int64_t r, int) {
     int v = P->active[r];
     const auto& verts = sv[r];
@@ -642,20 +643,32 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
       c[2 * rows + i] = out[2 * rows + i] / (ell * ell);
     }
     if (o->viscous) {                       // vertex-only LS, f and g decoupled (Sec. 2.3)
-      int K = nterms(o->visc_degree);
-      std::vector<double> B((size_t)N * K);
-      for (int j = 0; j < N; ++j) {
-        taylor(xv[2 * j], xv[2 * j + 1], o->visc_degree, p, nullptr, nullptr);
-        for (int k = 0; k < K; ++k) B[j + (size_t)k * N] = p[k];
-      }
-      const int targ[5][2] = {{1, -1}, {2, -1}, {3, -1}, {4, -1}, {5, -1}};
+      // Degree visc_degree, dropping by one while a weight of the rows used (first and second
+      // derivatives, l_v-scaled) exceeds visc_coef_max: nearly unisolvent vertex sets give
+      // exploding weights and a locally unstable viscous operator (down to degree 2).
       std::vector<double> q(5 * (size_t)N);
-      if (N >= K) {
-        ls_rows(N, K, B, targ, 5, q.data());
-      } else {            // fewer stencil vertices than basis terms: minimum-norm solution
-        const int t1[5] = {1, 2, 3, 4, 5};
-        pinv_rows_svd(N, K, B, t1, 5, q.data());
+      int degz = o->visc_degree;
+      for (;;) {
+        int K = nterms(degz);
+        std::vector<double> B((size_t)N * K);
+        for (int j = 0; j < N; ++j) {
+          taylor(xv[2 * j], xv[2 * j + 1], degz, p, nullptr, nullptr);
+          for (int k = 0; k < K; ++k) B[j + (size_t)k * N] = p[k];
+        }
+        if (N >= K) {
+          const int targ[5][2] = {{1, -1}, {2, -1}, {3, -1}, {4, -1}, {5, -1}};
+          ls_rows(N, K, B, targ, 5, q.data());
+        } else {          // fewer stencil vertices than basis terms: minimum-norm solution
+          const int t1[5] = {1, 2, 3, 4, 5};
+          pinv_rows_svd(N, K, B, t1, 5, q.data());
+        }
+        double big = 0;
+        for (double x : q) big = std::max(big, std::fabs(x));
+        if (big <= o->visc_coef_max || degz <= 2) break;
+        --degz;
+        visc_fallbacks++;
       }
+      P->visc_degree[r] = degz;
       double* e = &P->visc_coef[P->visc_cptr[r]];
       double l2 = ell * ell;
       for (int j = 0; j < N; ++j) {           // rows over interleaved (f_j, g_j)
@@ -673,6 +686,7 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
     return err.st;
   }
   P->degree_fallbacks = fallbacks.load();
+  P->visc_fallbacks = visc_fallbacks.load();
 
   // ---- flux edges and their stencils / weights
   {
@@ -784,6 +798,7 @@ void hfd_default_options(hfd_options* o) {
   o->sens_hi = 0.79;
   o->sv_rtol = 1e-13;
   o->div_cond_min = 1e-12;
+  o->visc_coef_max = 8.0;
   o->harten = 0.1;
   o->cfl = 0.3;
 }
@@ -836,6 +851,7 @@ Arr lookup(const Prep* P, const char* name) {
   if (s == "div_coef") return D(P->div_coef, true);
   if (s == "div_degree") return I(P->div_degree);
   if (s == "visc_coef") return D(P->visc_coef, true);
+  if (s == "visc_degree") return I(P->visc_degree);
   if (s == "lmin") return D(P->lmin, false);
   return Arr{nullptr, -1, 0, false};
 }
@@ -851,7 +867,7 @@ hfd_status hfd_prep_concat(const hfd_prep* const* preps, int32_t n, hfd_prep** o
     if (o.viscous != o0.viscous || o.gamma != o0.gamma || o.mu != o0.mu || o.prandtl != o0.prandtl ||
         o.R_gas != o0.R_gas || o.weno_eps != o0.weno_eps || o.sens_lo != o0.sens_lo ||
         o.sens_hi != o0.sens_hi || o.harten != o0.harten || o.cfl != o0.cfl ||
-        o.precision != o0.precision) {
+        o.precision != o0.precision || o.visc_coef_max != o0.visc_coef_max) {
       hfd::set_error("hfd_prep_concat: member %d has different physical/numerical options", k);
       return HFD_ERR_ARG;
     }
@@ -891,6 +907,7 @@ hfd_status hfd_prep_concat(const hfd_prep* const* preps, int32_t n, hfd_prep** o
     addv(B->div_vidx, P.div_vidx, vo);
     addv(B->div_eidx, P.div_eidx, eo);
     B->div_degree.insert(B->div_degree.end(), P.div_degree.begin(), P.div_degree.end());
+    B->visc_degree.insert(B->visc_degree.end(), P.visc_degree.begin(), P.visc_degree.end());
     B->div_coef.insert(B->div_coef.end(), P.div_coef.begin(), P.div_coef.end());
     B->visc_coef.insert(B->visc_coef.end(), P.visc_coef.begin(), P.visc_coef.end());
     addv(B->flux_edges, P.flux_edges, eo);
@@ -913,6 +930,7 @@ hfd_status hfd_prep_concat(const hfd_prep* const* preps, int32_t n, hfd_prep** o
     }
     B->member_box.insert(B->member_box.end(), {x0, x1, y0, y1});
     B->degree_fallbacks += P.degree_fallbacks;
+    B->visc_fallbacks += P.visc_fallbacks;
     B->prep_seconds += P.prep_seconds;
     voff += P.nv;
     eoff += P.nedges();

@@ -31,6 +31,7 @@ struct Prep {
   std::vector<double> div_coef;
   std::vector<int64_t> visc_cptr;              // start of each vertex's 3*2N block
   std::vector<double> visc_coef;
+  std::vector<int32_t> visc_degree;            // degree kept per active vertex (viscous)
   // edges whose flux the divergence reads (ascending edge index) and their interpolation data
   std::vector<int32_t> flux_edges;             // Ef
   std::vector<int32_t> stencil;                // 6*Ef, input ids [i-2 .. i+3]
@@ -45,6 +46,7 @@ struct Prep {
   int32_t nmember = 1;
   std::vector<double> member_box;
   int64_t degree_fallbacks = 0;
+  int64_t visc_fallbacks = 0;
   double prep_seconds = 0;
 
   int64_t nedges() const { return (int64_t)edges.size() / 2; }

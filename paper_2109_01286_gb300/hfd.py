@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("R_gas", ctypes.c_double), ("weno_eps", ctypes.c_double),
                 ("sens_lo", ctypes.c_double), ("sens_hi", ctypes.c_double),
                 ("sv_rtol", ctypes.c_double), ("div_cond_min", ctypes.c_double),
-                ("harten", ctypes.c_double), ("cfl", ctypes.c_double)]
+                ("harten", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("visc_coef_max", ctypes.c_double)]
 
 
 class MeshDesc(ctypes.Structure):
@@ -67,7 +68,7 @@ class MeshStats(ctypes.Structure):
                 ("div_nv_max", ctypes.c_int32), ("div_ne_max", ctypes.c_int32),
                 ("rank_hist", ctypes.c_int64 * 16), ("div_degree_fallbacks", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("prep_seconds", ctypes.c_double),
-                ("nmember", ctypes.c_int32)]
+                ("nmember", ctypes.c_int32), ("visc_degree_fallbacks", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -149,7 +150,7 @@ def _desc(mesh):
 
 
 _INT_ARRAYS = {"edges", "flux_edges", "stencil", "rank", "active", "div_vptr", "div_vidx",
-               "div_eptr", "div_eidx", "div_degree"}
+               "div_eptr", "div_eidx", "div_degree", "visc_degree"}
 
 
 class Prep:

@@ -81,6 +81,28 @@ def test_host_prep_viscous_rows_match_oracle(pkg, n):
     assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max()
 
 
+def test_host_prep_viscous_degree_drop_matches_oracle(pkg):
+    """R6b on both sides: the default bound on the 48 x 48 torus (a handful of drops) and a
+    tight bound on 16 x 16 (a quarter of the vertices drop) give the same degrees and rows."""
+    from gpu_helpers import oracle_blocks
+    m = synth.jittered_grid(48, 48, 2 * np.pi, 2 * np.pi, seed=3)
+    topo = oracle.build_topology(m)
+    opts = oracle.Options(viscous=True, mu=0.01)
+    want = np.array([oracle.visc_rows(m, topo, v, opts)[2] for v in range(len(m["x"]))])
+    prep = pkg.Prep(m, viscous=True, mu=0.01)
+    got = prep.get("visc_degree")
+    np.testing.assert_array_equal(got, want)
+    assert 0 < np.sum(got < 4) < 0.01 * len(got)
+    m = synth.jittered_grid(16, 16, 2 * np.pi, 2 * np.pi, seed=3)
+    kw = dict(viscous=True, mu=0.01, visc_coef_max=1.5)
+    P = oracle.prepare(m, oracle.Options(**kw))
+    prep = pkg.Prep(m, **kw)
+    np.testing.assert_array_equal(prep.get("visc_degree"), P.visc_degree)
+    assert len(set(P.visc_degree.tolist())) >= 2
+    ref = oracle_blocks(P, len(m["x"]))["visc_coef"]
+    assert np.abs(prep.get("visc_coef") - ref).max() < 1e-10 * np.abs(ref).max()
+
+
 def test_host_prep_with_ghosts_matches_oracle(pkg):
     m = synth.jittered_box_with_ghosts(20, 16, (0.0, 1.0), (0.0, 1.0), 5, seed=2)
     P = oracle.prepare(m)

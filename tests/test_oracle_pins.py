@@ -349,20 +349,50 @@ def test_divergence_rows_exact_for_degree5_fields(c1):
         np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-9 * np.abs(want).max())
 
 
+def _check_visc_rows_exact(m, topo, v, opts, rng):
+    verts, rows, deg = oracle.visc_rows(m, topo, int(v), opts)
+    K = (deg + 1) * (deg + 2) // 2
+    a, b = np.zeros(15), np.zeros(15)
+    a[:K], b[:K] = rng.standard_normal(K), rng.standard_normal(K)
+    z = []
+    for u in verts:
+        r = H.disp(m, int(v), int(u))
+        p = oracle.taylor_basis(r[0], r[1], 4)[0]
+        z += [p @ a, p @ b]
+    np.testing.assert_allclose(rows @ np.array(z), [a[1] + b[2], a[3] + b[4], a[4] + b[5]],
+                               rtol=1e-9, atol=1e-9)
+    return deg
+
+
 def test_viscous_rows_exact_for_quartics(c1):
     m, topo = c1
     opts = oracle.Options()
     rng = np.random.default_rng(12)
     for v in rng.choice(len(m["x"]), 5, replace=False):
-        verts, rows = oracle.visc_rows(m, topo, int(v), opts)
-        a, b = rng.standard_normal(15), rng.standard_normal(15)
-        z = []
-        for u in verts:
-            r = H.disp(m, int(v), int(u))
-            p = oracle.taylor_basis(r[0], r[1], 4)[0]
-            z += [p @ a, p @ b]
-        np.testing.assert_allclose(rows @ np.array(z), [a[1] + b[2], a[3] + b[4], a[4] + b[5]],
-                                   rtol=1e-9, atol=1e-9)
+        assert _check_visc_rows_exact(m, topo, v, opts, rng) == 4
+
+
+def test_viscous_rows_degree_drop_on_nearly_unisolvent_sets():
+    """R6b: on a 48 x 48 jittered torus a few two-level vertex sets are nearly unisolvent for
+    the 15 quartic terms (fitted weights up to ~30 in l_v-scaled units, against a median ~1).
+    Those vertices drop to degree 3 and must then be exact for cubics; all others stay quartic
+    and exact for quartics; every kept row set respects the weight bound."""
+    m = synth.jittered_grid(48, 48, 2 * np.pi, 2 * np.pi, seed=3)
+    topo = oracle.build_topology(m)
+    opts = oracle.Options()
+    rng = np.random.default_rng(13)
+    degs = np.array([oracle.visc_rows(m, topo, v, opts)[2] for v in range(len(m["x"]))])
+    dropped = np.nonzero(degs < 4)[0]
+    assert 0 < len(dropped) < 0.01 * len(degs)
+    for v in dropped[:4]:
+        assert _check_visc_rows_exact(m, topo, v, opts, rng) == degs[v]
+        loose = oracle.Options(visc_coef_max=np.inf)
+        verts, rows4, d4 = oracle.visc_rows(m, topo, int(v), loose)
+        ell = np.mean([np.linalg.norm(H.disp(m, int(v), int(u))) for u in topo["nbrs"][v]])
+        assert d4 == 4
+        assert max(np.abs(rows4[0]).max() * ell, np.abs(rows4[1:]).max() * ell ** 2) > 8.0
+    for v in rng.choice(np.nonzero(degs == 4)[0], 3, replace=False):
+        _check_visc_rows_exact(m, topo, v, opts, rng)
 
 
 # ------------------------------------------------------------------ whole residual
