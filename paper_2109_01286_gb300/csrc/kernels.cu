@@ -70,6 +70,11 @@ __device__ __forceinline__ void st4(float* p, const float* v) {
   *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// Loads of the coefficient, weight and index streams: each element is read once per stage, in
+// address order within a vertex's block (divergence) or across a warp's edges (edge weights).
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) { return __ldg(p); }
+
 // ------------------------------------------------------------------ physics (Sec. 2.3)
 template <typename T>
 __device__ __forceinline__ T pressure(const T* w, T g1) {
@@ -198,7 +203,7 @@ __device__ __forceinline__ void vertex_body(int v, int V, const double* __restri
     T t[4] = {T(w[4 * i]), T(w[4 * i + 1]), T(w[4 * i + 2]), T(w[4 * i + 3])};
     st4(ua + 4 * i, t);
   }
-  T g1 = T(ph.gamma - 1.0);
+  T g1 = phys_g1<T>(ph);
   T q[4] = {T(w[0]), T(w[1]), T(w[2]), T(w[3])};
   T ir = T(1) / q[0];
   T u = q[1] * ir, vv = q[2] * ir;
@@ -276,11 +281,11 @@ __device__ __forceinline__ void edge_body(int e, int Ef, const int32_t* __restri
                                           const T* __restrict__ w3, const T* __restrict__ Ua,
                                           T* __restrict__ h, const Phys& ph) {
   if (e >= Ef) return;
-  const T g1 = T(ph.gamma - 1.0);
+  const T g1 = phys_g1<T>(ph);
   int s[6];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) s[k] = __ldg(sten + (size_t)k * Ef + e);
-  T nx = __ldg(nrm + e), ny = __ldg(nrm + Ef + e);
+  for (int k = 0; k < 6; ++k) s[k] = ld_stream(sten + (size_t)k * Ef + e);
+  T nx = ld_stream(nrm + e), ny = ld_stream(nrm + Ef + e);
   T wi[4], wj[4];
   {
     T a[12];
@@ -305,15 +310,15 @@ __device__ __forceinline__ void edge_body(int e, int Ef, const int32_t* __restri
     T a[12];
     ld12(Ua + (size_t)s[k] * 12, a);
     if (k <= 4) {
-      T wv = __ldg(w5 + (size_t)(3 * k) * Ef + e), wx = __ldg(w5 + (size_t)(3 * k + 1) * Ef + e);
-      T wy = __ldg(w5 + (size_t)(3 * k + 2) * Ef + e);
+      T wv = ld_stream(w5 + (size_t)(3 * k) * Ef + e), wx = ld_stream(w5 + (size_t)(3 * k + 1) * Ef + e);
+      T wy = ld_stream(w5 + (size_t)(3 * k + 2) * Ef + e);
 #pragma unroll
       for (int r = 0; r < 4; ++r) W5L[r] = fma(wv, a[r], fma(wx, a[4 + r], fma(wy, a[8 + r], W5L[r])));
     }
     if (k >= 1) {
-      T wv = __ldg(w5 + (size_t)(15 + 3 * (k - 1)) * Ef + e);
-      T wx = __ldg(w5 + (size_t)(16 + 3 * (k - 1)) * Ef + e);
-      T wy = __ldg(w5 + (size_t)(17 + 3 * (k - 1)) * Ef + e);
+      T wv = ld_stream(w5 + (size_t)(15 + 3 * (k - 1)) * Ef + e);
+      T wx = ld_stream(w5 + (size_t)(16 + 3 * (k - 1)) * Ef + e);
+      T wy = ld_stream(w5 + (size_t)(17 + 3 * (k - 1)) * Ef + e);
 #pragma unroll
       for (int r = 0; r < 4; ++r) W5R[r] = fma(wv, a[r], fma(wx, a[4 + r], fma(wy, a[8 + r], W5R[r])));
     }
@@ -337,12 +342,12 @@ __device__ __forceinline__ void edge_body(int e, int Ef, const int32_t* __restri
       else           { u0 = cf[5][q]; u1 = cf[4][q]; u2 = cf[3][q]; u3 = cf[2][q]; u4 = cf[1][q]; }
       float b[3];
       smoothness(u0, u1, u2, u3, u4, b);
-      float eps = (float)ph.eps;
+      float eps = ph.epsf;
       float s0 = eps + b[0], s1 = eps + b[1], s2 = eps + b[2];
       s0 *= s0; s1 *= s1; s2 *= s2;
       float t0 = 0.0625f * s1 * s2, t1 = 0.625f * s0 * s2, t2 = 0.3125f * s0 * s1;
       float S = t0 + t1 + t2;
-      float mlo = t0 - (float)ph.sens_lo * S, mhi = (float)ph.sens_hi * S - t0;
+      float mlo = t0 - ph.sens_lof * S, mhi = ph.sens_hif * S - t0;
       unsigned bit = 1u << (side * 4 + q);
       if (!(mlo > 0.f && mhi > 0.f)) rough |= bit;
       if (!(fabsf(mlo) > kGuard * S && fabsf(mhi) > kGuard * S)) amb |= bit;
@@ -378,11 +383,11 @@ __device__ __forceinline__ void edge_body(int e, int Ef, const int32_t* __restri
         bool smooth = (t[0] > ph.sens_lo * S) && (t[0] < ph.sens_hi * S);
         if (smooth) continue;
         const T* w = w3 + (size_t)(9 * side) * Ef + e;
-        T c1 = __ldg(w) * cq[0] + __ldg(w + Ef) * cq[1] + __ldg(w + 2 * (size_t)Ef) * cq[2];
-        T c2 = __ldg(w + 3 * (size_t)Ef) * cq[1] + __ldg(w + 4 * (size_t)Ef) * cq[2] +
-               __ldg(w + 5 * (size_t)Ef) * cq[3];
-        T c3 = __ldg(w + 6 * (size_t)Ef) * cq[2] + __ldg(w + 7 * (size_t)Ef) * cq[3] +
-               __ldg(w + 8 * (size_t)Ef) * cq[4];
+        T c1 = ld_stream(w) * cq[0] + ld_stream(w + Ef) * cq[1] + ld_stream(w + 2 * (size_t)Ef) * cq[2];
+        T c2 = ld_stream(w + 3 * (size_t)Ef) * cq[1] + ld_stream(w + 4 * (size_t)Ef) * cq[2] +
+               ld_stream(w + 5 * (size_t)Ef) * cq[3];
+        T c3 = ld_stream(w + 6 * (size_t)Ef) * cq[2] + ld_stream(w + 7 * (size_t)Ef) * cq[3] +
+               ld_stream(w + 8 * (size_t)Ef) * cq[4];
         double iS = 1.0 / S;
         C[q] = T((t[0] * (double)c1 + t[1] * (double)c2 + t[2] * (double)c3) * iS);
       }
@@ -397,7 +402,7 @@ __device__ __forceinline__ void edge_body(int e, int Ef, const int32_t* __restri
 #pragma unroll
     for (int q = 0; q < 4; ++q) wside[1][q] = wj[q];
   T hq[4];
-  roe_flux(wside[0], wside[1], nx, ny, g1, T(ph.harten), hq);
+  roe_flux(wside[0], wside[1], nx, ny, g1, phys_harten<T>(ph), hq);
   st4(h + (size_t)e * 4, hq);
 }
 
@@ -496,8 +501,8 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
     // vertex entries, two per lane per iteration so that both entries' loads are in flight
     // before their multiply-adds (the same per-lane summation order as one at a time)
     auto vtx = [&](int j, const T* f, const T* fv) {
-      T c0f = __ldg(c + j), c0g = __ldg(c + N + j), cxf = __ldg(c + 2 * N + j);
-      T cxg = __ldg(c + 3 * N + j), cyf = __ldg(c + 4 * N + j), cyg = __ldg(c + 5 * N + j);
+      T c0f = ld_stream(c + j), c0g = ld_stream(c + N + j), cxf = ld_stream(c + 2 * N + j);
+      T cxg = ld_stream(c + 3 * N + j), cyf = ld_stream(c + 4 * N + j), cyg = ld_stream(c + 5 * N + j);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         acc[q] = fma(c0g, f[4 + q], fma(c0f, f[q], acc[q]));
@@ -505,8 +510,8 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
         acc[8 + q] = fma(cyg, f[4 + q], fma(cyf, f[q], acc[8 + q]));
       }
       if (VISC) {
-        c0f = __ldg(cz + j); c0g = __ldg(cz + N + j); cxf = __ldg(cz + 2 * N + j);
-        cxg = __ldg(cz + 3 * N + j); cyf = __ldg(cz + 4 * N + j); cyg = __ldg(cz + 5 * N + j);
+        c0f = ld_stream(cz + j); c0g = ld_stream(cz + N + j); cxf = ld_stream(cz + 2 * N + j);
+        cxg = ld_stream(cz + 3 * N + j); cyf = ld_stream(cz + 4 * N + j); cyg = ld_stream(cz + 5 * N + j);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           acc[q] = fma(-c0g, fv[4 + q], fma(-c0f, fv[q], acc[q]));
@@ -517,7 +522,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
     };
     int j = lane;
     for (; j + G < N; j += 2 * G) {
-      int u0 = __ldg(vidx + n0 + j), u1 = __ldg(vidx + n0 + j + G);
+      int u0 = ld_stream(vidx + n0 + j), u1 = ld_stream(vidx + n0 + j + G);
       T f0[8], f1[8], g0[8], g1[8];
       ld8(FG + (size_t)u0 * 8, f0);
       ld8(FG + (size_t)u1 * 8, f1);
@@ -529,7 +534,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
       vtx(j + G, f1, g1);
     }
     if (j < N) {
-      int u0 = __ldg(vidx + n0 + j);
+      int u0 = ld_stream(vidx + n0 + j);
       T f0[8], g0[8];
       ld8(FG + (size_t)u0 * 8, f0);
       if (VISC) ld8(FGv + (size_t)u0 * 8, g0);
@@ -538,7 +543,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
     int m0 = __ldg(eptr + r), M = __ldg(eptr + r + 1) - m0;
     const T* d = ce + 3 * (size_t)m0;
     auto edg = [&](int jj, const T* hv) {
-      T d0 = __ldg(d + jj), dx = __ldg(d + M + jj), dy = __ldg(d + 2 * M + jj);
+      T d0 = ld_stream(d + jj), dx = ld_stream(d + M + jj), dy = ld_stream(d + 2 * M + jj);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         acc[q] = fma(d0, hv[q], acc[q]);
@@ -548,7 +553,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
     };
     j = lane;
     for (; j + G < M; j += 2 * G) {
-      int e0 = __ldg(eidx + m0 + j), e1 = __ldg(eidx + m0 + j + G);
+      int e0 = ld_stream(eidx + m0 + j), e1 = ld_stream(eidx + m0 + j + G);
       T h0[4], h1[4];
       ld4(h + (size_t)e0 * 4, h0);
       ld4(h + (size_t)e1 * 4, h1);
@@ -556,7 +561,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
       edg(j + G, h1);
     }
     if (j < M) {
-      int e0 = __ldg(eidx + m0 + j);
+      int e0 = ld_stream(eidx + m0 + j);
       T h0[4];
       ld4(h + (size_t)e0 * 4, h0);
       edg(j, h0);

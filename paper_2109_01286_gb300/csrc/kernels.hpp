@@ -10,7 +10,25 @@ namespace hfd {
 struct Phys {
   double gamma, eps, sens_lo, sens_hi, harten, cfl;
   double mu, kappa, R_gas;      // viscous model (Sec. 2.3; constant mu, kappa = mu c_p / Pr)
+  double g1;                    // gamma - 1
+  // the same constants rounded once to FP32 on the host (no FP64 conversions in FP32 kernels)
+  float g1f, epsf, sens_lof, sens_hif, hartenf;
+  void finish() {
+    g1 = gamma - 1.0;
+    g1f = (float)g1;
+    epsf = (float)eps;
+    sens_lof = (float)sens_lo;
+    sens_hif = (float)sens_hi;
+    hartenf = (float)harten;
+  }
 };
+
+template <typename T> __host__ __device__ inline T phys_g1(const Phys& p);
+template <> __host__ __device__ inline double phys_g1<double>(const Phys& p) { return p.g1; }
+template <> __host__ __device__ inline float phys_g1<float>(const Phys& p) { return p.g1f; }
+template <typename T> __host__ __device__ inline T phys_harten(const Phys& p);
+template <> __host__ __device__ inline double phys_harten<double>(const Phys& p) { return p.harten; }
+template <> __host__ __device__ inline float phys_harten<float>(const Phys& p) { return p.hartenf; }
 
 // Device arrays of one mesh in internal numbering.  Coefficient and flux arrays hold elements
 // of the path's bulk precision T (double or float), addressed through void pointers here.
