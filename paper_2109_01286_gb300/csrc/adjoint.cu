@@ -68,19 +68,19 @@ __device__ __forceinline__ double press(const double* w, double g1) {
   return g1 * (w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0]);
 }
 
-// One thread per flux edge: hbar = -(D^T mu) at the edge, then the reverse of Alg. 1 and the
-// Roe flux; writes the sensitivities of the 12 values of the 6 stencil nodes to Ge[e][72].
-__global__ void __launch_bounds__(128) k_adj_edge(
-    int Ef, int V, const int32_t* __restrict__ sten, const double* __restrict__ nrm,
-    const double* __restrict__ w5, const double* __restrict__ w3, const double* __restrict__ Ua,
-    const int32_t* __restrict__ eptr, const double* __restrict__ ce,
-    const int32_t* __restrict__ te_ptr, const int32_t* __restrict__ te_row,
-    const int32_t* __restrict__ te_pos, const double* __restrict__ mu, double* __restrict__ Ge,
-    Phys ph) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= Ef) return;
+// Shared front of the edge reverse pass: hbar = -(D^T mu) at the edge, the stencil, the end
+// states and the FP32 sensor decisions exactly as k_edge takes them (bit side*4+q of `rough`:
+// 3-node branch; of `amb`: inside the guard band, re-decided in FP64).
+__device__ __forceinline__ void adj_edge_front(
+    int e, int Ef, int V, const int32_t* __restrict__ sten, const double* __restrict__ nrm,
+    const double* __restrict__ Ua, const int32_t* __restrict__ eptr,
+    const double* __restrict__ ce, const int32_t* __restrict__ te_ptr,
+    const int32_t* __restrict__ te_row, const int32_t* __restrict__ te_pos,
+    const double* __restrict__ mu, const Phys& ph, double* hb, int* s, double& nx, double& ny,
+    double* wi, double* wj, unsigned& rough, unsigned& amb) {
+  const double g1 = ph.g1;
   // ---- hbar = -(D^T mu)_e
-  double hb[4] = {0, 0, 0, 0};
+  for (int q = 0; q < 4; ++q) hb[q] = 0.0;
   for (int t = te_ptr[e]; t < te_ptr[e + 1]; ++t) {
     int r = te_row[t], j = te_pos[t];
     int m0 = eptr[r], M = eptr[r + 1] - m0;
@@ -90,16 +90,13 @@ __global__ void __launch_bounds__(128) k_adj_edge(
       hb[q] -= d0 * mu[(size_t)q * V + r] + dx * mu[(size_t)(4 + q) * V + r] +
                dy * mu[(size_t)(8 + q) * V + r];
   }
-  double* ge = Ge + (size_t)e * 72;
-  for (int i = 0; i < 72; ++i) ge[i] = 0.0;
-  const double g1 = ph.gamma - 1.0;
-  int s[6];
   for (int k = 0; k < 6; ++k) s[k] = sten[(size_t)k * Ef + e];
-  double nx = nrm[e], ny = nrm[Ef + e];
-  double wi[4], wj[4];
+  nx = nrm[e];
+  ny = nrm[Ef + e];
   for (int r = 0; r < 4; ++r) { wi[r] = Ua[(size_t)s[2] * 12 + r]; wj[r] = Ua[(size_t)s[3] * 12 + r]; }
   // ---- forward: FP32 sensor exactly as k_edge
-  unsigned rough = 0, amb = 0;
+  rough = 0;
+  amb = 0;
   {
     float fi[4] = {(float)wi[0], (float)wi[1], (float)wi[2], (float)wi[3]};
     float fj[4] = {(float)wj[0], (float)wj[1], (float)wj[2], (float)wj[3]};
@@ -132,19 +129,25 @@ __global__ void __launch_bounds__(128) k_adj_edge(
         for (int j = 0; j < 5; ++j) uu[j] = cf[side == 0 ? j : 5 - j][q];
         float b[3];
         smooth3(uu[0], uu[1], uu[2], uu[3], uu[4], b);
-        float eps = (float)ph.eps;
+        float eps = ph.epsf;
         float s0 = eps + b[0], s1 = eps + b[1], s2 = eps + b[2];
         s0 *= s0; s1 *= s1; s2 *= s2;
         float t0 = 0.0625f * s1 * s2, t1 = 0.625f * s0 * s2, t2 = 0.3125f * s0 * s1;
         float S = t0 + t1 + t2;
-        float mlo = t0 - (float)ph.sens_lo * S, mhi = (float)ph.sens_hi * S - t0;
+        float mlo = t0 - ph.sens_lof * S, mhi = ph.sens_hif * S - t0;
         unsigned bit = 1u << (side * 4 + q);
         if (!(mlo > 0.f && mhi > 0.f)) rough |= bit;
         if (!(fabsf(mlo) > 1e-3f * S && fabsf(mhi) > 1e-3f * S)) amb |= bit;
       }
   }
+}
+
+// FP64 5-node sums of both sides in conservative variables (the forward interpolation).
+__device__ __forceinline__ void adj_edge_w5(int e, int Ef, const int* s, const double* __restrict__ w5,
+                                            const double* __restrict__ Ua, double (*W5)[4]) {
   // ---- forward in FP64: 5-node conservative sums, sides with re-decided / 3-node components
-  double W5[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  for (int side = 0; side < 2; ++side)
+    for (int r = 0; r < 4; ++r) W5[side][r] = 0.0;
   for (int k = 0; k < 6; ++k) {
     const double* a = Ua + (size_t)s[k] * 12;
     for (int side = 0; side < 2; ++side) {
@@ -156,6 +159,112 @@ __global__ void __launch_bounds__(128) k_adj_edge(
       for (int r = 0; r < 4; ++r) W5[side][r] += wv * a[r] + wx * a[4 + r] + wy * a[8 + r];
     }
   }
+}
+
+// One thread per flux edge, edges whose sides both took the 5-node branch: the reverse of the
+// Roe flux and of the 5-node sums; each node's 12 sensitivities are formed in registers and
+// stored once to Ge[e][72].  Edges with a 3-node or re-decided component are appended to
+// `list` for k_adj_edge_full (the order of the list does not matter: each edge writes only
+// its own Ge row).
+__global__ void __launch_bounds__(128, 3) k_adj_edge(
+    int Ef, int V, const int32_t* __restrict__ sten, const double* __restrict__ nrm,
+    const double* __restrict__ w5, const double* __restrict__ w3, const double* __restrict__ Ua,
+    const int32_t* __restrict__ eptr, const double* __restrict__ ce,
+    const int32_t* __restrict__ te_ptr, const int32_t* __restrict__ te_row,
+    const int32_t* __restrict__ te_pos, const double* __restrict__ mu, double* __restrict__ Ge,
+    Phys ph, int32_t* __restrict__ list, int32_t* __restrict__ count) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Ef) return;
+  double hb[4], nx, ny, wi[4], wj[4];
+  int s[6];
+  unsigned rough, amb;
+  adj_edge_front(e, Ef, V, sten, nrm, Ua, eptr, ce, te_ptr, te_row, te_pos, mu, ph, hb, s, nx, ny,
+                 wi, wj, rough, amb);
+  if (rough | amb) {
+    list[atomicAdd(count, 1)] = e;
+    return;
+  }
+  double* ge = Ge + (size_t)e * 72;
+  const double g1 = ph.g1;
+  double W5[2][4];
+  adj_edge_w5(e, Ef, s, w5, Ua, W5);
+  bool fb0 = !(W5[0][0] > 0.0) || !(press(W5[0], g1) > 0.0);
+  bool fb1 = !(W5[1][0] > 0.0) || !(press(W5[1], g1) > 0.0);
+  double wl[4], wr[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    wl[r] = fb0 ? wi[r] : W5[0][r];
+    wr[r] = fb1 ? wj[r] : W5[1][r];
+  }
+  double b0[4] = {0, 0, 0, 0}, b1[4] = {0, 0, 0, 0};
+  adj::roe_flux_vjp(wl, wr, nx, ny, g1, ph.harten, hb, b0, b1);
+  double wib[4] = {0, 0, 0, 0}, wjb[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    if (fb0) { wib[r] = b0[r]; b0[r] = 0.0; }
+    if (fb1) { wjb[r] = b1[r]; b1[r] = 0.0; }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double g[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) g[i] = 0.0;
+    if (k <= 4) {
+      double wv = w5[(size_t)(3 * k) * Ef + e], wx = w5[(size_t)(3 * k + 1) * Ef + e];
+      double wy = w5[(size_t)(3 * k + 2) * Ef + e];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        g[r] += wv * b0[r];
+        g[4 + r] += wx * b0[r];
+        g[8 + r] += wy * b0[r];
+      }
+    }
+    if (k >= 1) {
+      double wv = w5[(size_t)(15 + 3 * (k - 1)) * Ef + e];
+      double wx = w5[(size_t)(16 + 3 * (k - 1)) * Ef + e];
+      double wy = w5[(size_t)(17 + 3 * (k - 1)) * Ef + e];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        g[r] += wv * b1[r];
+        g[4 + r] += wx * b1[r];
+        g[8 + r] += wy * b1[r];
+      }
+    }
+    if (k == 2)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) g[r] += wib[r];
+    if (k == 3)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) g[r] += wjb[r];
+    double2* o = reinterpret_cast<double2*>(ge + 12 * k);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o[i] = make_double2(g[2 * i], g[2 * i + 1]);
+  }
+}
+
+// One thread per listed flux edge (a 3-node or re-decided component on some side): the full
+// reverse of Alg. 1 and the Roe flux; writes the sensitivities of the 12 values of the 6
+// stencil nodes to Ge[e][72].
+__global__ void __launch_bounds__(128) k_adj_edge_full(
+    int Ef, int V, const int32_t* __restrict__ sten, const double* __restrict__ nrm,
+    const double* __restrict__ w5, const double* __restrict__ w3, const double* __restrict__ Ua,
+    const int32_t* __restrict__ eptr, const double* __restrict__ ce,
+    const int32_t* __restrict__ te_ptr, const int32_t* __restrict__ te_row,
+    const int32_t* __restrict__ te_pos, const double* __restrict__ mu, double* __restrict__ Ge,
+    Phys ph, const int32_t* __restrict__ list, const int32_t* __restrict__ count) {
+  int li = blockIdx.x * blockDim.x + threadIdx.x;
+  if (li >= *count) return;
+  int e = list[li];
+  double hb[4], nx, ny, wi[4], wj[4];
+  int s[6];
+  unsigned rough, amb;
+  adj_edge_front(e, Ef, V, sten, nrm, Ua, eptr, ce, te_ptr, te_row, te_pos, mu, ph, hb, s, nx, ny,
+                 wi, wj, rough, amb);
+  double* ge = Ge + (size_t)e * 72;
+  const double g1 = ph.g1;
+  double W5[2][4];
+  adj_edge_w5(e, Ef, s, w5, Ua, W5);
+  for (int i = 0; i < 72; ++i) ge[i] = 0.0;
   adj::RoeState rs;
   double L[4][4];
   adj::roe_state(wi, wj, g1, rs);
@@ -426,6 +535,10 @@ hfd_status build_transposes(hfd_mesh* m) {
   if ((st = upload_vec(m, &m->adj_Ge, zeros)) != HFD_OK) return st;
   zeros.assign((size_t)12 * V, 0.0);
   if ((st = upload_vec(m, &m->adj_B1, zeros)) != HFD_OK) return st;
+  std::vector<int32_t> izeros((size_t)Ef + 1, 0);
+  if ((st = upload_vec(m, &m->adj_list, izeros)) != HFD_OK) return st;
+  izeros.assign(1, 0);
+  if ((st = upload_vec(m, &m->adj_count, izeros)) != HFD_OK) return st;
   if ((st = upload_vec(m, &m->adj_B2, zeros)) != HFD_OK) return st;
   return HFD_OK;
 }
@@ -436,10 +549,17 @@ hfd_status residual_vjp(hfd_mesh* m, const double* Us, const double* mu, double*
                         double cg, cudaStream_t s) {
   const hfd::DevMesh& d = m->dm;
   ACK(hfd::launch_vertex(d, Us, m->ph, s));          // AoS copy of the stage state
+  // edges with both sides on the 5-node branch, then the listed remainder
+  ACK(cudaMemsetAsync(m->adj_count, 0, sizeof(int32_t), s));
   hfd::k_adj_edge<<<(d.Ef + 127) / 128, 128, 0, s>>>(
       d.Ef, d.V, d.sten, (const double*)d.nrm, (const double*)d.w5, (const double*)d.w3,
       (const double*)d.Ua, d.eptr, (const double*)d.ce, m->adj_te_ptr, m->adj_te_row,
-      m->adj_te_pos, mu, m->adj_Ge, m->ph);
+      m->adj_te_pos, mu, m->adj_Ge, m->ph, m->adj_list, m->adj_count);
+  ACK(cudaGetLastError());
+  hfd::k_adj_edge_full<<<(d.Ef + 127) / 128, 128, 0, s>>>(
+      d.Ef, d.V, d.sten, (const double*)d.nrm, (const double*)d.w5, (const double*)d.w3,
+      (const double*)d.Ua, d.eptr, (const double*)d.ce, m->adj_te_ptr, m->adj_te_row,
+      m->adj_te_pos, mu, m->adj_Ge, m->ph, m->adj_list, m->adj_count);
   ACK(cudaGetLastError());
   hfd::k_adj_vertex<<<(d.V + 127) / 128, 128, 0, s>>>(
       d.V, Us, d.vptr, (const double*)d.cv, m->adj_tv_ptr, m->adj_tv_row, m->adj_tv_pos,

@@ -32,10 +32,12 @@ struct hfd_mesh {
   std::vector<void*> allocs;
   int device = 0;
   // adjoint (built on the first hfd_adjoint call): transposed divergence / stencil lists,
-  // per-edge node sensitivities [Ef][72], two adjoint stage buffers 12 x V
+  // per-edge node sensitivities [Ef][72], two adjoint stage buffers 12 x V, the list of edges
+  // with a 3-node or re-decided component and its length
   int32_t *adj_tv_ptr = nullptr, *adj_tv_row = nullptr, *adj_tv_pos = nullptr;
   int32_t *adj_te_ptr = nullptr, *adj_te_row = nullptr, *adj_te_pos = nullptr;
   int32_t *adj_ts_ptr = nullptr, *adj_ts_ent = nullptr;
   double *adj_Ge = nullptr, *adj_B1 = nullptr, *adj_B2 = nullptr;
+  int32_t *adj_list = nullptr, *adj_count = nullptr;
 };
 
