@@ -85,6 +85,18 @@ typedef struct {
   double visc_coef_max;    /* viscous vertex-only LS: the degree drops by one (down to 2)
                               while a first- or second-derivative weight, in coordinates
                               scaled by the mean incident edge length, exceeds this       [8] */
+  /* Device memory of a mesh (no counterpart in the paper).  NULL: cudaMalloc / cudaFree.
+   * Otherwise every device block a mesh holds comes from dev_alloc(bytes, alloc_ctx) on the
+   * current device and goes back through dev_free(ptr, alloc_ctx) in hfd_mesh_destroy, after a
+   * device synchronisation (a caching allocator may hand the block out again at once).
+   * dev_alloc must return memory aligned to 256 bytes, or NULL when it cannot; the library
+   * then fails with HFD_ERR_CUDA.  Both or neither must be set (else HFD_ERR_ARG).
+   * hfd_residual_static allocates nothing either way.                                 [NULL] */
+  void* (*dev_alloc)(size_t bytes, void* alloc_ctx);
+  void (*dev_free)(void* ptr, void* alloc_ctx);
+  void* alloc_ctx;
+  int32_t flux;            /* Riemann solver of the edge flux (Sec. 2.3 after Alg. 1; the paper
+                              does not name one): 0 Roe with Harten's fix, 1 Rusanov       [0] */
 } hfd_options;
 
 typedef struct {

@@ -13,11 +13,11 @@ open are tagged R1..R20 and listed in the repository's design notes.
 from .hfd_oracle import (Options, build_topology, edge_stencil, taylor_basis, five_node_weights,
                          three_node_weights, edge_geometry, vertex_stencil, div_rows, visc_rows,
                          prepare, euler_flux, viscous_flux, roe_average, eigenvectors,
-                         weno_weights, roe_flux, ghost_fill, residual, ssp_rk3, step, cfl_dt,
+                         weno_weights, roe_flux, rusanov_flux, riemann_flux, ghost_fill, residual, ssp_rk3, step, cfl_dt,
                          vertex_areas)
 
 __all__ = ["Options", "build_topology", "edge_stencil", "taylor_basis", "five_node_weights",
            "three_node_weights", "edge_geometry", "vertex_stencil", "div_rows", "visc_rows",
            "prepare", "euler_flux", "viscous_flux", "roe_average", "eigenvectors",
-           "weno_weights", "roe_flux", "ghost_fill", "residual", "ssp_rk3", "step", "cfl_dt",
+           "weno_weights", "roe_flux", "rusanov_flux", "riemann_flux", "ghost_fill", "residual", "ssp_rk3", "step", "cfl_dt",
            "vertex_areas"]

@@ -44,6 +44,7 @@ class Options:
     div_cond_min: float = 1e-12   # R6: fall back to degree-1 below this sigma_min/sigma_max
     visc_coef_max: float = 8.0    # R6b: viscous LS degree drops while a scaled weight exceeds this
     harten: float = 0.1           # R9: entropy-fix width delta = harten * c_roe
+    flux: str = "roe"             # R9: Riemann solver, "roe" or "rusanov"
     viscous: bool = False
     mu: float = 0.0
     prandtl: float = 0.72
@@ -510,6 +511,29 @@ def roe_flux(wl, wr, nx, ny, gamma, harten=0.1):
         - 0.5 * np.moveaxis(diss, -1, 0)
 
 
+def rusanov_flux(wl, wr, nx, ny, gamma):
+    """Rusanov's (local Lax-Friedrichs) flux along n, the alternative Riemann solver of R9:
+    h = (F_n(wl) + F_n(wr)) / 2 - s (wr - wl) / 2, with s the larger of |u_n| + c over the
+    two states.  Complex-step safe (comparisons on real parts)."""
+    def speed(w):
+        un = (w[1] * nx + w[2] * ny) / w[0]
+        c = np.sqrt(gamma * pressure(w, gamma) / w[0])
+        return np.where(np.real(un) < 0, -un, un) + c
+    sl, sr = speed(wl), speed(wr)
+    s = np.where(np.real(sl) >= np.real(sr), sl, sr)
+    return 0.5 * (normal_flux(wl, nx, ny, gamma) + normal_flux(wr, nx, ny, gamma)) \
+        - 0.5 * s * (wr - wl)
+
+
+def riemann_flux(wl, wr, nx, ny, opts):
+    """The edge's numerical flux h (Sec. 2.3, after Alg. 1) with the solver of opts.flux."""
+    if opts.flux == "rusanov":
+        return rusanov_flux(wl, wr, nx, ny, opts.gamma)
+    if opts.flux != "roe":
+        raise ValueError(f"unknown Riemann solver {opts.flux!r}")
+    return roe_flux(wl, wr, nx, ny, opts.gamma, opts.harten)
+
+
 # --------------------------------------------------------------------------- residual
 
 def ghost_fill(mesh, U):
@@ -572,7 +596,7 @@ def edge_values_from_stencil(P, W, opts, diag=None):
 def edge_flux_from_stencil(P, W, opts):
     """Numerical flux h (4, Ee) of every needed edge from its gathered stencil states."""
     wl, wr = edge_values_from_stencil(P, W, opts)
-    return roe_flux(wl, wr, P.normal[:, 0], P.normal[:, 1], opts.gamma, opts.harten)
+    return riemann_flux(wl, wr, P.normal[:, 0], P.normal[:, 1], opts)
 
 
 def residual(mesh, P, U, opts=None, diag=None):
@@ -585,7 +609,7 @@ def residual(mesh, P, U, opts=None, diag=None):
     V = U.shape[1]
     F, G = euler_flux(U[0:4], g)
     wl, wr = edge_values(P, U, opts, diag)
-    h = roe_flux(wl, wr, P.normal[:, 0], P.normal[:, 1], g, opts.harten)   # (4, Ee)
+    h = riemann_flux(wl, wr, P.normal[:, 0], P.normal[:, 1], opts)   # (4, Ee)
     E = len(P.topo["edges"])
     Rm = np.zeros((12, V), dtype=U.dtype)
     for q in range(4):

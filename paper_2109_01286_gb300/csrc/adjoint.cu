@@ -471,9 +471,7 @@ template <typename T>
 hfd_status upload_vec(hfd_mesh* m, T** dst, const std::vector<T>& v) {
   void* p = nullptr;
   size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
-  ACK(cudaMalloc(&p, bytes));
-  m->allocs.push_back(p);
-  m->stats.device_bytes += (int64_t)bytes;
+  ACK(mesh_malloc(m, &p, bytes));
   if (!v.empty()) ACK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
   *dst = static_cast<T*>(p);
   return HFD_OK;
@@ -577,8 +575,8 @@ extern "C" hfd_status hfd_adjoint(hfd_mesh* m, const double* U_n, const double* 
     return HFD_ERR_ARG;
   }
   const hfd::DevMesh& d = m->dm;
-  if (d.precision != 0 || d.viscous || d.G != 0 || d.nmember != 1) {
-    set_error("hfd_adjoint: built for FP64 inviscid single meshes without ghosts");
+  if (d.precision != 0 || d.viscous || d.G != 0 || d.nmember != 1 || m->ph.flux != 0) {
+    set_error("hfd_adjoint: built for FP64 inviscid single meshes without ghosts, Roe flux");
     return HFD_ERR_UNSUPPORTED;
   }
   if (!m->adj_Ge) {

@@ -48,9 +48,7 @@ template <typename T>
 hfd_status dev_upload(hfd_mesh* m, void** dst, const std::vector<T>& src) {
   size_t bytes = std::max<size_t>(src.size() * sizeof(T), 16);
   void* p = nullptr;
-  CK(cudaMalloc(&p, bytes));
-  m->allocs.push_back(p);
-  m->stats.device_bytes += (int64_t)bytes;
+  CK(mesh_malloc(m, &p, bytes));
   if (!src.empty()) CK(cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
   *dst = p;
   return HFD_OK;
@@ -59,10 +57,8 @@ hfd_status dev_upload(hfd_mesh* m, void** dst, const std::vector<T>& src) {
 hfd_status dev_alloc(hfd_mesh* m, void** dst, size_t bytes) {
   void* p = nullptr;
   bytes = std::max<size_t>(bytes, 16);
-  CK(cudaMalloc(&p, bytes));
+  CK(mesh_malloc(m, &p, bytes));
   CK(cudaMemset(p, 0, bytes));
-  m->allocs.push_back(p);
-  m->stats.device_bytes += (int64_t)bytes;
   *dst = p;
   return HFD_OK;
 }
@@ -268,6 +264,7 @@ hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
   m->ph.mu = o.mu;
   m->ph.R_gas = o.R_gas;
   m->ph.kappa = o.mu * (o.gamma * o.R_gas / (o.gamma - 1.0)) / o.prandtl;
+  m->ph.flux = o.flux;
   m->ph.finish();
   // ---- stats
   hfd_mesh_stats& s = m->stats;
@@ -405,7 +402,7 @@ void hfd_mesh_destroy(hfd_mesh* m) {
   cudaSetDevice(m->device);
   drop_graphs(m);
   if (m->cap) cudaStreamDestroy(m->cap);
-  for (void* p : m->allocs) cudaFree(p);
+  mesh_free_all(m);
   cudaSetDevice(prev);
   delete m;
 }

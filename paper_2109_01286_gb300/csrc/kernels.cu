@@ -138,34 +138,46 @@ __device__ __forceinline__ void normal_flux(const T* w, T nx, T ny, T g1, T* f) 
   f[3] = (w[3] + p) * un;
 }
 
+// Reciprocal square roots: the CUDA math library's rsqrt (FP64: at most 1 ulp) and the FP32
+// hardware approximation.
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
 // Roe's flux with Harten's entropy fix on all waves (Riemann flux, Sec. 2.3 after Alg. 1).
 // The primitive quantities of each side (1/rho, u, v, p, H) are formed once and shared by the
-// Roe average and the two normal fluxes.
+// Roe average and the two normal fluxes.  One reciprocal square root per side gives sqrt(rho)
+// and 1/rho, one more gives c and 1/c; the entropy fix multiplies by 1/(2 delta) =
+// half_inv_harten / c with half_inv_harten = 1/(2 harten).
 template <typename T>
 __device__ __forceinline__ void roe_flux(const T* wl, const T* wr, T nx, T ny, T g1, T harten,
-                                         T* hq) {
-  T irl = T(1) / wl[0], irr = T(1) / wr[0];
+                                         T half_inv_harten, T* hq) {
+  T sl = rsqrt_t(wl[0]), sr = rsqrt_t(wr[0]);
+  T irl = sl * sl, irr = sr * sr;
+  T rl = wl[0] * sl, rr = wr[0] * sr;
   T ul = wl[1] * irl, vl = wl[2] * irl, ur = wr[1] * irr, vr = wr[2] * irr;
   T pl = g1 * (wl[3] - T(0.5) * (wl[1] * ul + wl[2] * vl));
   T pr = g1 * (wr[3] - T(0.5) * (wr[1] * ur + wr[2] * vr));
   T Hl = (wl[3] + pl) * irl, Hr = (wr[3] + pr) * irr;
-  T rl = sqrt(wl[0]), rr = sqrt(wr[0]);
   T fl_ = rl / (rl + rr), fr_ = T(1) - fl_;
   T u = fl_ * ul + fr_ * ur, v = fl_ * vl + fr_ * vr, H = fl_ * Hl + fr_ * Hr;
-  T c = sqrt(g1 * (H - T(0.5) * (u * u + v * v)));
-  T L[4][4];
-  left_ev(u, v, c, nx, ny, g1, L);
-  T d[4] = {wr[0] - wl[0], wr[1] - wl[1], wr[2] - wl[2], wr[3] - wl[3]};
+  T c2 = g1 * (H - T(0.5) * (u * u + v * v));
+  T ic = rsqrt_t(c2), c = c2 * ic;
   T qn = u * nx + v * ny;
+  // wave strengths L (w_r - w_l) from the primitive jumps: by the Roe property of the averages
+  // they equal the left-eigenvector products (Roe's own form of the solver)
+  T rho = rl * rr, dp = pr - pl, drho = wr[0] - wl[0];
+  T dun = (ur - ul) * nx + (vr - vl) * ny, dut = (vr - vl) * nx - (ur - ul) * ny;
+  T ic2 = ic * ic, hc2 = T(0.5) * ic2;
+  T rcd = rho * c * dun;
+  T a[4] = {(dp - rcd) * hc2, drho - dp * ic2, rho * dut, (dp + rcd) * hc2};
   T lam[4] = {qn - c, qn, qn, qn + c};
-  T del = harten * c;
+  T del = harten * c, i2del = half_inv_harten * ic;
   T k[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    T a = L[i][0] * d[0] + L[i][1] * d[1] + L[i][2] * d[2] + L[i][3] * d[3];
     T al = fabs(lam[i]);
-    if (al < del) al = (lam[i] * lam[i] + del * del) / (T(2) * del);
-    k[i] = al * a;
+    if (al < del) al = (lam[i] * lam[i] + del * del) * i2del;
+    k[i] = al * a[i];
   }
   T diss[4];
   right_apply(u, v, H, c, nx, ny, k, diss);
@@ -174,6 +186,30 @@ __device__ __forceinline__ void roe_flux(const T* wl, const T* wr, T nx, T ny, T
   T fr[4] = {wr[0] * unr, wr[1] * unr + pr * nx, wr[2] * unr + pr * ny, (wr[3] + pr) * unr};
 #pragma unroll
   for (int i = 0; i < 4; ++i) hq[i] = T(0.5) * (fl[i] + fr[i]) - T(0.5) * diss[i];
+}
+
+// Rusanov's (local Lax-Friedrichs) flux along n: the mean of the two normal fluxes minus half
+// the larger of |u_n| + c over the two states times the jump (the alternative solver).
+template <typename T>
+__device__ __forceinline__ void rusanov_flux(const T* wl, const T* wr, T nx, T ny, T g1, T* hq) {
+  T irl = T(1) / wl[0], irr = T(1) / wr[0];
+  T unl = (wl[1] * nx + wl[2] * ny) * irl, unr = (wr[1] * nx + wr[2] * ny) * irr;
+  T pl = g1 * (wl[3] - T(0.5) * (wl[1] * wl[1] + wl[2] * wl[2]) * irl);
+  T pr = g1 * (wr[3] - T(0.5) * (wr[1] * wr[1] + wr[2] * wr[2]) * irr);
+  T gam = g1 + T(1);
+  T sl = fabs(unl) + sqrt(gam * pl * irl), sr = fabs(unr) + sqrt(gam * pr * irr);
+  T s = sl >= sr ? sl : sr;
+  T fl[4] = {wl[0] * unl, wl[1] * unl + pl * nx, wl[2] * unl + pl * ny, (wl[3] + pl) * unl};
+  T fr[4] = {wr[0] * unr, wr[1] * unr + pr * nx, wr[2] * unr + pr * ny, (wr[3] + pr) * unr};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) hq[i] = T(0.5) * (fl[i] + fr[i]) - T(0.5) * s * (wr[i] - wl[i]);
+}
+
+// rho > 0 and p > 0 (R16), without a division: p = (gamma-1)(E - |m|^2/(2 rho)) has the sign
+// of E rho - |m|^2/2 when rho > 0.
+template <typename T>
+__device__ __forceinline__ bool admissible(const T* w) {
+  return w[0] > T(0) && w[3] * w[0] - T(0.5) * (w[1] * w[1] + w[2] * w[2]) > T(0);
 }
 
 // Jiang-Shu smoothness indicators of the three sub-stencils of u0..u4 (uniform WENO5, R2).
@@ -395,23 +431,27 @@ __device__ __forceinline__ void edge_body(int e, int Ef, const int32_t* __restri
     }
   }
   // positivity (R16): fall back to the end state of that side
-  if (!(wside[0][0] > T(0)) || !(pressure(wside[0], g1) > T(0)))
+  if (!admissible(wside[0]))
 #pragma unroll
     for (int q = 0; q < 4; ++q) wside[0][q] = wi[q];
-  if (!(wside[1][0] > T(0)) || !(pressure(wside[1], g1) > T(0)))
+  if (!admissible(wside[1]))
 #pragma unroll
     for (int q = 0; q < 4; ++q) wside[1][q] = wj[q];
   T hq[4];
-  roe_flux(wside[0], wside[1], nx, ny, g1, phys_harten<T>(ph), hq);
+  if (ph.flux == 1)
+    rusanov_flux(wside[0], wside[1], nx, ny, g1, hq);
+  else
+    roe_flux(wside[0], wside[1], nx, ny, g1, phys_harten<T>(ph), phys_half_inv_harten<T>(ph), hq);
   st4(h + (size_t)e * 4, hq);
 }
 
 // Resident blocks of 128 threads the compiler must allow: 3 for FP64 data (<= 170 registers; an
-// explicit bound of 1 lets it take ~214 and lose a block), 4 for FP32 data (5 would spill).
+// explicit bound of 1 lets it take ~214 and lose a block), 5 for FP32 data (96 registers, an
+// 8-byte spill; 4 percent faster than 4 blocks on the four-quadrant 1024x1024 step).
 template <typename T>
 struct EdgeOcc { static constexpr int kMinBlocks = 3; };
 template <>
-struct EdgeOcc<float> { static constexpr int kMinBlocks = 4; };
+struct EdgeOcc<float> { static constexpr int kMinBlocks = 5; };
 
 template <typename T>
 __global__ void __launch_bounds__(128, EdgeOcc<T>::kMinBlocks) k_edge(int Ef, const int32_t* __restrict__ sten,
@@ -658,11 +698,12 @@ __global__ void __launch_bounds__(256) k_dtmin(int A, int V, const double* __res
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   double val = INFINITY;
   if (v < A) {
+    // lmin / (|u| + c) = lmin rho / (|m| + sqrt(gamma (gamma-1) (E rho - |m|^2 / 2))): one
+    // division instead of three (rho c = sqrt(gamma p rho), p rho = (gamma-1)(E rho - |m|^2/2))
     double rho = U[v], m = U[(size_t)V + v], n = U[2 * (size_t)V + v], E = U[3 * (size_t)V + v];
-    double uu = m / rho, vv = n / rho;
-    double p = (gamma - 1.0) * (E - 0.5 * rho * (uu * uu + vv * vv));
-    double s = sqrt(uu * uu + vv * vv) + sqrt(gamma * p / rho);
-    val = lmin[v] / s;
+    double q = m * m + n * n;
+    double sr = sqrt(q) + sqrt(gamma * (gamma - 1.0) * (E * rho - 0.5 * q));
+    val = lmin[v] * rho / sr;
     if (!(val > 0.0)) val = INFINITY;   // non-physical states do not set the step
   }
   int first = blockIdx.x * blockDim.x, last = min(A - 1, first + (int)blockDim.x - 1);

@@ -10,11 +10,16 @@ namespace hfd {
 struct Phys {
   double gamma, eps, sens_lo, sens_hi, harten, cfl;
   double mu, kappa, R_gas;      // viscous model (Sec. 2.3; constant mu, kappa = mu c_p / Pr)
+  int flux;                     // 0 Roe (Harten's fix), 1 Rusanov
   double g1;                    // gamma - 1
   // the same constants rounded once to FP32 on the host (no FP64 conversions in FP32 kernels)
   float g1f, epsf, sens_lof, sens_hif, hartenf;
+  double half_inv_harten;       // 1 / (2 harten): the entropy fix's 1/(2 delta) is this over c
+  float half_inv_hartenf;
   void finish() {
     g1 = gamma - 1.0;
+    half_inv_harten = 0.5 / harten;   // +inf for harten = 0, where the fix never applies
+    half_inv_hartenf = (float)half_inv_harten;
     g1f = (float)g1;
     epsf = (float)eps;
     sens_lof = (float)sens_lo;
@@ -29,6 +34,9 @@ template <> __host__ __device__ inline float phys_g1<float>(const Phys& p) { ret
 template <typename T> __host__ __device__ inline T phys_harten(const Phys& p);
 template <> __host__ __device__ inline double phys_harten<double>(const Phys& p) { return p.harten; }
 template <> __host__ __device__ inline float phys_harten<float>(const Phys& p) { return p.hartenf; }
+template <typename T> __host__ __device__ inline T phys_half_inv_harten(const Phys& p);
+template <> __host__ __device__ inline double phys_half_inv_harten<double>(const Phys& p) { return p.half_inv_harten; }
+template <> __host__ __device__ inline float phys_half_inv_harten<float>(const Phys& p) { return p.half_inv_hartenf; }
 
 // Device arrays of one mesh in internal numbering.  Coefficient and flux arrays hold elements
 // of the path's bulk precision T (double or float), addressed through void pointers here.

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <map>
 #include <utility>
 #include <vector>
@@ -41,3 +42,34 @@ struct hfd_mesh {
   int32_t *adj_list = nullptr, *adj_count = nullptr;
 };
 
+// A device block of the mesh: from the caller's allocator (hfd_options.dev_alloc) if there is
+// one, else cudaMalloc; recorded for hfd_mesh_destroy.  Blocks must be 256-byte aligned.
+inline cudaError_t mesh_malloc(hfd_mesh* m, void** p, size_t bytes) {
+  *p = nullptr;
+  if (m->opts.dev_alloc) {
+    void* q = m->opts.dev_alloc(bytes, m->opts.alloc_ctx);
+    if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+      m->opts.dev_free(q, m->opts.alloc_ctx);
+      return cudaErrorMisalignedAddress;
+    }
+    *p = q;
+  } else {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  m->allocs.push_back(*p);
+  m->stats.device_bytes += (int64_t)bytes;
+  return cudaSuccess;
+}
+
+// Releases every block of the mesh (the current device must be the mesh's).
+inline void mesh_free_all(hfd_mesh* m) {
+  if (m->opts.dev_alloc) {
+    cudaDeviceSynchronize();     // no kernel may still use a block the allocator reuses
+    for (void* p : m->allocs) m->opts.dev_free(p, m->opts.alloc_ctx);
+  } else {
+    for (void* p : m->allocs) cudaFree(p);
+  }
+  m->allocs.clear();
+}

@@ -38,6 +38,28 @@ class HfdError(RuntimeError):
         self.status = status
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def _torch_alloc(nbytes, ctx):
+    import torch
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device())
+    except Exception:                 # out of memory: the library reports HFD_ERR_CUDA
+        return None
+
+
+def _torch_free(ptr, ctx):
+    import torch
+    torch.cuda.caching_allocator_delete(ptr)
+
+
+# module-level so that the C function pointers outlive every mesh that holds them
+TORCH_ALLOC = _ALLOC_FN(_torch_alloc)
+TORCH_FREE = _FREE_FN(_torch_free)
+
+
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("div_degree", ctypes.c_int32),
                 ("visc_degree", ctypes.c_int32), ("viscous", ctypes.c_int32),
@@ -47,7 +69,8 @@ class Options(ctypes.Structure):
                 ("sens_lo", ctypes.c_double), ("sens_hi", ctypes.c_double),
                 ("sv_rtol", ctypes.c_double), ("div_cond_min", ctypes.c_double),
                 ("harten", ctypes.c_double), ("cfl", ctypes.c_double),
-                ("visc_coef_max", ctypes.c_double)]
+                ("visc_coef_max", ctypes.c_double), ("dev_alloc", _ALLOC_FN),
+                ("dev_free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("flux", ctypes.c_int32)]
 
 
 class MeshDesc(ctypes.Structure):
@@ -110,12 +133,20 @@ def _ok(status, where):
 
 def options(**kw):
     """hfd_options with the library defaults, overridden by keyword (precision may be 'fp64' or
-    'fp32'; booleans are accepted for viscous/renumber)."""
+    'fp32', flux 'roe' or 'rusanov'; booleans are accepted for viscous/renumber;
+    allocator='torch' takes the mesh's device memory from PyTorch's caching allocator)."""
     o = Options()
     _lib.hfd_default_options(ctypes.byref(o))
+    alloc = kw.pop("allocator", None)
+    if alloc == "torch":              # device blocks from PyTorch's caching allocator
+        o.dev_alloc, o.dev_free = TORCH_ALLOC, TORCH_FREE
+    elif alloc not in (None, "cuda"):
+        raise ValueError(f"allocator must be None, 'cuda' or 'torch', not {alloc!r}")
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": 0, "fp32": 1, "mixed": 1}[v]
+        if k == "flux" and isinstance(v, str):
+            v = {"roe": 0, "rusanov": 1}[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
         setattr(o, k, int(v) if isinstance(v, bool) else v)

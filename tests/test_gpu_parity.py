@@ -329,3 +329,87 @@ def test_viscous_steps_parity_taylor_green():
     out = mesh.export_state(X).cpu().numpy()
     err = rel_l2_groups(out, ref)
     assert max(err) < 1e-11, err
+
+
+def test_caller_allocator_holds_the_mesh_and_gives_identical_results(c1):
+    """hfd_options.dev_alloc / dev_free with PyTorch's caching allocator: the mesh's device
+    blocks are counted by torch, released on destroy, and the results are bit-identical."""
+    import gc
+    pkg = _hfd()
+    m, P, U = c1
+    a = pkg.Mesh(m)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    b = pkg.Mesh(m, allocator="torch")
+    held = torch.cuda.memory_allocated() - before
+    assert held >= b.stats.device_bytes > 0
+    np.testing.assert_array_equal(_residual(a, U), _residual(b, U))
+    Xa = a.import_state(torch.from_numpy(U).cuda())
+    Xb = b.import_state(torch.from_numpy(U).cuda())
+    a.steps(Xa, 0.0, 3)
+    b.steps(Xb, 0.0, 3)
+    torch.testing.assert_close(Xa, Xb, rtol=0, atol=0)
+    lam = torch.ones_like(Xa)
+    dt = a.last_dt()
+    torch.testing.assert_close(a.adjoint(Xa, lam, dt=dt), b.adjoint(Xb, lam, dt=dt), rtol=0, atol=0)
+    total = b.stats.device_bytes
+    mid = torch.cuda.memory_allocated()
+    del b
+    gc.collect()
+    torch.cuda.synchronize()
+    assert mid - torch.cuda.memory_allocated() >= total
+
+
+@pytest.mark.parametrize("case", ["c1", "quad"])
+def test_rusanov_residual_kernel_parity(case, request):
+    """The alternative Riemann solver (hfd_options.flux = 1) against the oracle's Rusanov flux,
+    FP64 kernel parity, on the vortex and on the four-quadrant mesh with ghosts."""
+    pkg = _hfd()
+    m, P, U = request.getfixturevalue(case)
+    mesh = _kernel_mesh(pkg, m, P, flux="rusanov")
+    R = _residual(mesh, U)
+    opts = oracle.Options(flux="rusanov")
+    R_ref = oracle.residual(m, P, U.copy(), opts)
+    keep = np.setdiff1d(P.active, near_threshold_vertices(m, P, U, opts))
+    err = rel_l2_groups(R, R_ref, keep)
+    assert max(err) < TOL_FP64, err
+    R_roe = oracle.residual(m, P, U.copy())
+    assert max(rel_l2_groups(R_roe, R_ref)) > 1e3 * TOL_FP64      # the solvers differ
+
+
+def test_positivity_fallback_kernel_parity(c1):
+    """R16 on a near-vacuum state: rho = p = 0.01 everywhere, random derivatives of size 0.05.
+    The values are uniform, so every sensor decision is the 5-node branch, and the 5-node
+    values overshoot below zero on about 6% of the sides.  Those sides fall back to the
+    edge's end state, on the GPU as in the oracle."""
+    pkg = _hfd()
+    m, P, _ = c1
+    rng = np.random.default_rng(17)
+    U = synth.uniform_state(m, rho=0.01, p=0.01)
+    U[4:] = 0.05 * rng.standard_normal(U[4:].shape)
+    diag = {}
+    R_ref = oracle.residual(m, P, U.copy(), diag=diag)
+    assert 100 < diag["positivity_fallbacks"] < 0.5 * 2 * len(P.edges)
+    R = _residual(_kernel_mesh(pkg, m, P), U)
+    err = rel_l2_groups(R, R_ref)
+    assert max(err) < TOL_FP64, err
+
+
+@pytest.mark.parametrize("n", [7, 9])
+def test_tiny_periodic_mesh_kernel_parity(n):
+    """Degenerate size: a 7x7 / 9x9 torus (49 / 81 vertices, less than one thread block),
+    where the two-level sets and the 6-node stencils wrap around most of the mesh.  Smooth
+    random data; vertices whose sensor value lies within 1e-9 of a threshold are excluded."""
+    pkg = _hfd()
+    m = synth.jittered_grid(n, n, 1.0, 1.0, seed=9)
+    P = oracle.prepare(m)
+    rng = np.random.default_rng(19)
+    U = synth.uniform_state(m)
+    U[:4] *= 1.0 + 0.05 * rng.random((4, len(m["x"])))
+    U[4:] = 0.05 * rng.standard_normal(U[4:].shape)
+    R = _residual(_kernel_mesh(pkg, m, P), U)
+    R_ref = oracle.residual(m, P, U.copy())
+    keep = np.setdiff1d(P.active, near_threshold_vertices(m, P, U, P.opts))
+    assert len(keep) > 0.8 * len(P.active)
+    err = rel_l2_groups(R, R_ref, keep)
+    assert max(err) < TOL_FP64, err

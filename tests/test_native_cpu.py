@@ -112,6 +112,22 @@ def test_host_prep_with_ghosts_matches_oracle(pkg):
     np.testing.assert_array_equal(prep.get("active"), P.active)
 
 
+def test_allocator_and_flux_options_are_checked(pkg):
+    with pytest.raises(ValueError):
+        pkg.options(allocator="malloc")
+    assert pkg.options(flux="rusanov").flux == 1 and pkg.options().flux == 0
+    m = synth.jittered_grid(8, 8, 1.0, 1.0, seed=0)
+    d, keep = pkg.hfd._desc(m)
+    h = pkg.hfd._P()
+    ct = pkg.hfd.ctypes
+    bad = pkg.options(flux=2)
+    assert pkg.hfd._lib.hfd_prep_create(ct.byref(d), ct.byref(bad), ct.byref(h)) == 1
+    o = pkg.options(allocator="torch")
+    assert bool(o.dev_alloc) and bool(o.dev_free)
+    o.dev_free = pkg.hfd._FREE_FN()          # only one of the two callbacks: rejected
+    assert pkg.hfd._lib.hfd_prep_create(ct.byref(d), ct.byref(o), ct.byref(h)) == 1
+
+
 def test_invalid_meshes_are_rejected(pkg):
     m = synth.jittered_grid(6, 6, 1.0, 1.0, seed=0)
     bad = dict(m)

@@ -319,6 +319,36 @@ def test_roe_flux_consistency_and_supersonic_upwinding():
                                rtol=1e-13)
 
 
+def test_rusanov_flux_consistency_contact_and_dissipation():
+    """R9 alternative solver.  (1) h(w, w) = F_n(w).  (2) A stationary contact (u = 0, equal
+    p) carries a mass flux of exactly -s (rho_r - rho_l) / 2 with s = max(c_l, c_r): the
+    solver's known smearing of contacts.  (3) Linearised about w, dh/dw_r = (A_n(w) - s I) / 2
+    with s = |u_n| + c: the flux Jacobian A_n comes from a complex-step derivative of the
+    analytic normal flux, the dissipation from the definition."""
+    rng = np.random.default_rng(81)
+    g = 1.4
+    w = _state(rng)
+    np.testing.assert_allclose(oracle.rusanov_flux(w, w, 0.6, 0.8, g),
+                               H.normal_flux(w, 0.6, 0.8, g), rtol=1e-15)
+    wl = synth.prim_to_cons(1.0, 0.0, 0.3, 1.0)
+    wr = synth.prim_to_cons(0.25, 0.0, 0.3, 1.0)
+    h = oracle.rusanov_flux(wl, wr, 1.0, 0.0, g)
+    s = max(np.sqrt(g * 1.0 / 1.0), np.sqrt(g * 1.0 / 0.25))
+    assert abs(h[0] - (-0.5 * s * (0.25 - 1.0))) < 1e-15
+    nx, ny = 0.6, 0.8
+    A = np.zeros((4, 4))
+    J = np.zeros((4, 4))
+    for k in range(4):
+        wc = w.astype(complex)
+        wc[k] += 1e-30j
+        A[:, k] = H.normal_flux(wc, nx, ny, g).imag / 1e-30
+        J[:, k] = oracle.rusanov_flux(w.astype(complex), wc, nx, ny, g).imag / 1e-30
+    u, v = w[1] / w[0], w[2] / w[0]
+    p = (g - 1.0) * (w[3] - 0.5 * w[0] * (u * u + v * v))
+    sp = abs(u * nx + v * ny) + np.sqrt(g * p / w[0])
+    np.testing.assert_allclose(J, 0.5 * (A - sp * np.eye(4)), atol=1e-13)
+
+
 # ------------------------------------------------------------------ LS divergence (Sec. 2.3)
 
 def test_divergence_rows_exact_for_degree5_fields(c1):
