@@ -36,6 +36,10 @@ import synth  # noqa: E402
 METRIC = "vertex-stage updates/s"
 FP64_PEAK_FLOPS = 1.258e12       # GB300 FP64: 152 SMs x 2 DFMA/clk (ncu peak_sustained) x 2 x 2.07 GHz
 CPU_PATCH_N = 32                 # bounded oracle sample: 32 x 32 patch of the same workload
+# DRAM bytes (read + write) per launch on the default 1024 x 1024 workload, from one ncu capture
+# of the current kernels (profiles/traffic_four_quadrant_1024x1024.md); other sizes report null
+DRAM_TRAFFIC_1024 = {"k_div<double>": 3256.2e6, "k_edge<double>": 1090.7e6,
+                     "k_div<float>": 1682.0e6, "k_edge<float>": 580.0e6}
 
 
 def parse():
@@ -321,9 +325,12 @@ def run_native(args):
     r = results["fp64"]
     dom = max(r["kernels"], key=lambda k: r["kernels"][k]["share"])
     kd = r["kernels"][dom]
+    def traffic(name):
+        return DRAM_TRAFFIC_1024.get(name) if args.n == 1024 else None
     roof = {"kernel": f"k_{dom}<double>", "bound": "alu", "achieved": kd["tflops"],
             "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-            "frac": kd["tflops"] / (FP64_PEAK_FLOPS / 1e12), "traffic": None,
+            "frac": kd["tflops"] / (FP64_PEAK_FLOPS / 1e12), "traffic": traffic(f"k_{dom}<double>"),
+            "traffic_unit": "bytes per launch (ncu DRAM read + write)",
             "peak_source": "derived: ncu dfma peak_sustained 2/SM/clk x 152 SMs x 2 flop x 2.07 GHz "
                            "(MEASURED_PEAKS.json has no FP64 figure)",
             "hbm_gbs": kd["gbs"], "hbm_frac": kd["gbs"] / peak_hbm,
@@ -351,7 +358,9 @@ def run_native(args):
             "state_finite": f32["finite"],
             "roofline": {"kernel": f"k_{dom32}<float>", "bound": "hbm", "achieved": k32["gbs"],
                          "peak": peak_hbm, "unit": "GB/s", "frac": k32["gbs"] / peak_hbm,
-                         "traffic": None, "peak_source": peak_src},
+                         "traffic": traffic(f"k_{dom32}<float>"),
+                         "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+                         "peak_source": peak_src},
             "kernels": f32["kernels"]}},
         "state_finite": r["finite"],
         "gpu_launches": int(r["launches"]),
