@@ -9,6 +9,7 @@
 #include <map>
 #include <new>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.hpp"
@@ -42,6 +43,41 @@ uint64_t hilbert(uint32_t x, uint32_t y) {
     }
   }
   return d;
+}
+
+// Re-lays a divergence CSR (per vertex: `rows` SoA rows of n entries each, coef at
+// rows * ptr[r]) into chunks of hfd::kDivChunk entries: ptr becomes chunk offsets, idx is
+// padded to whole chunks with the vertex's first index, and each chunk holds its rows
+// contiguously ([row][kDivChunk]) with zero coefficients in the padding.  `coef2` (the viscous
+// rows, same shape as coef) follows the same layout.
+template <typename T>
+void chunk_rows(int A, std::vector<int32_t>& ptr, std::vector<int32_t>& idx, int rows,
+                std::vector<T>& coef, std::vector<T>* coef2) {
+  const int C = hfd::kDivChunk;
+  std::vector<int32_t> cptr(A + 1, 0);
+  for (int r = 0; r < A; ++r) cptr[r + 1] = cptr[r] + (ptr[r + 1] - ptr[r] + C - 1) / C;
+  std::vector<int32_t> cidx((size_t)C * cptr[A]);
+  std::vector<T> cc((size_t)rows * C * cptr[A], T(0)), cc2;
+  if (coef2) cc2.assign(cc.size(), T(0));
+  for (int r = 0; r < A; ++r) {
+    int n = ptr[r + 1] - ptr[r];
+    int nc = cptr[r + 1] - cptr[r];
+    for (int k = 0; k < nc * C; ++k) {
+      int j = k < n ? k : 0;
+      cidx[(size_t)C * cptr[r] + k] = n > 0 ? idx[ptr[r] + j] : 0;
+      if (k >= n) continue;
+      size_t dst = (size_t)rows * C * cptr[r] + (size_t)(k / C) * rows * C + k % C;
+      for (int row = 0; row < rows; ++row) {
+        size_t src = (size_t)rows * ptr[r] + (size_t)row * n + k;
+        cc[dst + (size_t)row * C] = coef[src];
+        if (coef2) cc2[dst + (size_t)row * C] = (*coef2)[src];
+      }
+    }
+  }
+  ptr.swap(cptr);
+  idx.swap(cidx);
+  coef.swap(cc);
+  if (coef2) coef2->swap(cc2);
 }
 
 template <typename T>
@@ -132,6 +168,12 @@ hfd_status upload_streams(hfd_mesh* m, const hfd::Prep& P, const std::vector<int
         }
     }
   }
+  m->stats.div_nnz = vptr[A] * 2 + eptr[A];
+  if (std::is_same<T, float>::value) {
+    // FP32 bulk: entries in chunks of 4 (hfd::kDivChunk), each chunk's rows contiguous
+    chunk_rows(A, vptr, vidx, 6, cv, P.opts.viscous ? &cvis : nullptr);
+    chunk_rows(A, eptr, eidx, 3, ce, static_cast<std::vector<T>*>(nullptr));
+  }
   TRY(dev_upload(m, (void**)&d.vptr, vptr));
   TRY(dev_upload(m, (void**)&d.eptr, eptr));
   TRY(dev_upload(m, (void**)&d.vidx, vidx));
@@ -144,7 +186,6 @@ hfd_status upload_streams(hfd_mesh* m, const hfd::Prep& P, const std::vector<int
   TRY(dev_alloc(m, &d.FG, V * 8 * sizeof(T)));
   if (P.opts.viscous) TRY(dev_alloc(m, &d.FGv, V * 8 * sizeof(T)));
   TRY(dev_alloc(m, &d.h, (size_t)Ef * 4 * sizeof(T)));
-  m->stats.div_nnz = vptr[A] * 2 + eptr[A];
   return HFD_OK;
 }
 

@@ -19,6 +19,8 @@
 
 #include <cstdint>
 
+#include <type_traits>
+
 #include "kernels.hpp"
 
 namespace hfd {
@@ -513,6 +515,86 @@ struct StageArgs {
   double a, b, dt_fixed;
 };
 
+// FP32-bulk gather of one vertex's divergence rows over the chunked layout: lane `lane` of
+// the group takes chunks lane, lane + G, ...; per chunk one int4 of indices, 6 (3 for edges)
+// float4 coefficient rows and 4 flux gathers, all independent loads.  Padding entries carry
+// zero coefficients.
+__device__ __forceinline__ float f4c(const float4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ int i4c(const int4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+template <int G, bool VISC>
+__device__ __forceinline__ void div_gather_chunked(
+    int r, int lane, const int32_t* __restrict__ vptr, const int32_t* __restrict__ vidx,
+    const int32_t* __restrict__ eptr, const int32_t* __restrict__ eidx,
+    const float* __restrict__ cv, const float* __restrict__ ce, const float* __restrict__ cvis,
+    const float* __restrict__ FG, const float* __restrict__ FGv, const float* __restrict__ h,
+    float* acc) {
+  static_assert(kDivChunk == 4, "float4 chunks");
+  const int c0 = __ldg(vptr + r), nc = __ldg(vptr + r + 1) - c0;
+  const int4* vi = reinterpret_cast<const int4*>(vidx) + c0;
+  const float4* cc = reinterpret_cast<const float4*>(cv) + 6 * (size_t)c0;
+  const float4* cz = VISC ? reinterpret_cast<const float4*>(cvis) + 6 * (size_t)c0 : nullptr;
+  for (int ch = lane; ch < nc; ch += G) {
+    const int4 u = __ldg(vi + ch);
+    float4 k[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) k[i] = __ldg(cc + 6 * ch + i);
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      float f[8];
+      ld8(FG + (size_t)i4c(u, q4) * 8, f);
+      const float c0f = f4c(k[0], q4), c0g = f4c(k[1], q4), cxf = f4c(k[2], q4);
+      const float cxg = f4c(k[3], q4), cyf = f4c(k[4], q4), cyg = f4c(k[5], q4);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] = fmaf(c0g, f[4 + q], fmaf(c0f, f[q], acc[q]));
+        acc[4 + q] = fmaf(cxg, f[4 + q], fmaf(cxf, f[q], acc[4 + q]));
+        acc[8 + q] = fmaf(cyg, f[4 + q], fmaf(cyf, f[q], acc[8 + q]));
+      }
+    }
+    if (VISC) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) k[i] = __ldg(cz + 6 * ch + i);
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        float f[8];
+        ld8(FGv + (size_t)i4c(u, q4) * 8, f);
+        const float c0f = f4c(k[0], q4), c0g = f4c(k[1], q4), cxf = f4c(k[2], q4);
+        const float cxg = f4c(k[3], q4), cyf = f4c(k[4], q4), cyg = f4c(k[5], q4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[q] = fmaf(-c0g, f[4 + q], fmaf(-c0f, f[q], acc[q]));
+          acc[4 + q] = fmaf(-cxg, f[4 + q], fmaf(-cxf, f[q], acc[4 + q]));
+          acc[8 + q] = fmaf(-cyg, f[4 + q], fmaf(-cyf, f[q], acc[8 + q]));
+        }
+      }
+    }
+  }
+  const int m0 = __ldg(eptr + r), mc = __ldg(eptr + r + 1) - m0;
+  const int4* ei = reinterpret_cast<const int4*>(eidx) + m0;
+  const float4* dd = reinterpret_cast<const float4*>(ce) + 3 * (size_t)m0;
+  for (int ch = lane; ch < mc; ch += G) {
+    const int4 e = __ldg(ei + ch);
+    const float4 d0 = __ldg(dd + 3 * ch), dx = __ldg(dd + 3 * ch + 1), dy = __ldg(dd + 3 * ch + 2);
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      float hv[4];
+      ld4(h + (size_t)i4c(e, q4) * 4, hv);
+      const float a0 = f4c(d0, q4), ax = f4c(dx, q4), ay = f4c(dy, q4);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] = fmaf(a0, hv[q], acc[q]);
+        acc[4 + q] = fmaf(ax, hv[q], acc[4 + q]);
+        acc[8 + q] = fmaf(ay, hv[q], acc[8 + q]);
+      }
+    }
+  }
+}
+
 template <typename T, int G, bool VISC>
 __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __restrict__ vptr,
                                          const int32_t* __restrict__ vidx,
@@ -534,7 +616,9 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
   T acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = T(0);
-  if (live) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (live) div_gather_chunked<G, VISC>(r, lane, vptr, vidx, eptr, eidx, cv, ce, cvis, FG, FGv, h, acc);
+  } else if (live) {
     int n0 = __ldg(vptr + r), N = __ldg(vptr + r + 1) - n0;
     const T* c = cv + 6 * (size_t)n0;
     const T* cz = VISC ? cvis + 6 * (size_t)n0 : nullptr;

@@ -38,6 +38,9 @@ template <typename T> __host__ __device__ inline T phys_half_inv_harten(const Ph
 template <> __host__ __device__ inline double phys_half_inv_harten<double>(const Phys& p) { return p.half_inv_harten; }
 template <> __host__ __device__ inline float phys_half_inv_harten<float>(const Phys& p) { return p.half_inv_hartenf; }
 
+// Divergence entries per chunk of the FP32-bulk layout (vector loads of 4 coefficients).
+constexpr int kDivChunk = 4;
+
 // Device arrays of one mesh in internal numbering.  Coefficient and flux arrays hold elements
 // of the path's bulk precision T (double or float), addressed through void pointers here.
 struct DevMesh {
@@ -54,7 +57,10 @@ struct DevMesh {
   void* w5 = nullptr;
   void* w3 = nullptr;
   // divergence CSR over active vertices; per-vertex SoA coefficient blocks:
-  // cv at 6*vptr[r]: d0F, d0G, dxF, dxG, dyF, dyG (each N long); ce at 3*eptr[r]: d0, dx, dy
+  // cv at 6*vptr[r]: d0F, d0G, dxF, dxG, dyF, dyG (each N long); ce at 3*eptr[r]: d0, dx, dy.
+  // FP32 bulk instead: vptr/eptr count chunks of kDivChunk entries, the index lists are padded
+  // to whole chunks, and each chunk holds its 6 (cv, cvis) or 3 (ce) rows of kDivChunk
+  // coefficients contiguously (zero in the padding)
   int32_t *vptr = nullptr, *vidx = nullptr, *eptr = nullptr, *eidx = nullptr;
   void* cv = nullptr;
   void* ce = nullptr;
