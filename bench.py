@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="four-quadrant",
-                    choices=["four-quadrant", "batched", "adjoint", "tgv"],
+                    choices=["four-quadrant", "batched", "adjoint", "tgv", "conservative"],
                     help="batched: 256 uneven isentropic-vortex meshes advanced together; "
-                         "adjoint: gradient of a 200-step vortex run, checked by differences")
+                         "adjoint: gradient of a 200-step vortex run, checked by differences; "
+                         "conservative: the four-quadrant line with median-dual value rows")
     ap.add_argument("--directions", type=int, default=64)
     ap.add_argument("--batch", type=int, default=256)
     return ap.parse_args()
@@ -220,7 +221,8 @@ def run_native(args):
     from paper_2109_01286_gb300 import Prep, replicas
     mesh, U = workload(args.n)
     t0 = time.perf_counter()
-    prep = Prep(mesh)
+    conservative = args.workload == "conservative"
+    prep = Prep(mesh, conservative=conservative)
     prep_s = time.perf_counter() - t0
     U_dev = torch.from_numpy(U).cuda()
     stream = torch.cuda.current_stream()
@@ -337,7 +339,9 @@ def run_native(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_name(args.n), "precision": "fp64",
+        "config": {"workload": workload_name(args.n) + (", conservative variant (median-dual "
+                                                        "value rows)" if conservative else ""),
+                   "precision": "fp64",
                    "step_input": "every timed step advances the initial state (device reset "
                                  "copy inside the timed region)",
                    "physical_vertices": r["stats"]["nactive"], "stored_vertices": r["stats"]["nv"],

@@ -97,6 +97,12 @@ typedef struct {
   void* alloc_ctx;
   int32_t flux;            /* Riemann solver of the edge flux (Sec. 2.3 after Alg. 1; the paper
                               does not name one): 0 Roe with Harten's fix, 1 Rusanov       [0] */
+  int32_t conservative;    /* 1: conservative variant, not in the paper (which names conservation
+                              as open, Sec. 4): the value rows become the median-dual finite
+                              volume divergence (1/|C_v|) sum_e +-|S_e| h_e, with S_e the
+                              dual-face area vector of edge e, and every edge's projection and
+                              Riemann flux is taken along S_e/|S_e|; the derivative rows stay
+                              least squares (with edge rows along S_e)                    [0] */
 } hfd_options;
 
 typedef struct {

@@ -45,6 +45,7 @@ class Options:
     visc_coef_max: float = 8.0    # R6b: viscous LS degree drops while a scaled weight exceeds this
     harten: float = 0.1           # R9: entropy-fix width delta = harten * c_roe
     flux: str = "roe"             # R9: Riemann solver, "roe" or "rusanov"
+    conservative: bool = False    # value equations as median-dual finite volumes (not in the paper)
     viscous: bool = False
     mu: float = 0.0
     prandtl: float = 0.72
@@ -227,6 +228,29 @@ def three_node_weights(rel3, near):
 # left side uses nodes 0..4 (i-2..i+2), right side mirrors: 5,4,3,2,1 (i+3..i-1)
 LEFT5, RIGHT5 = [0, 1, 2, 3, 4], [1, 2, 3, 4, 5]
 LEFT_ORDER, RIGHT_ORDER = [0, 1, 2, 3, 4], [5, 4, 3, 2, 1]
+def dual_faces(mesh, topo):
+    """Median-dual geometry of the conservative variant (the paper names conservation as open,
+    Sec. 4): for every edge (a, b), tail a < b, the dual-face area vector S_e = sum over the
+    triangles holding the edge of the segment from the edge midpoint to the triangle centroid,
+    turned by 90 degrees and oriented so that S_e . (x_b - x_a) > 0; and the median-dual cell
+    areas (R17).  Cached in topo."""
+    if "dual_S" in topo:
+        return topo["dual_S"], topo["dual_A"]
+    S = np.zeros((len(topo["edges"]), 2))
+    for t in np.asarray(mesh["tri"], dtype=np.int64):
+        x = [np.zeros(2), disp(mesh, t[0], t[1]), disp(mesh, t[0], t[2])]
+        g = (x[0] + x[1] + x[2]) / 3.0
+        for i, j in ((0, 1), (1, 2), (2, 0)):
+            a, b = (i, j) if t[i] < t[j] else (j, i)
+            seg = g - 0.5 * (x[i] + x[j])
+            nrm = np.array([seg[1], -seg[0]])
+            if nrm @ (x[b] - x[a]) < 0:
+                nrm = -nrm
+            S[topo["index"][(int(t[a]), int(t[b]))]] += nrm
+    topo["dual_S"], topo["dual_A"] = S, vertex_areas(mesh)
+    return topo["dual_S"], topo["dual_A"]
+
+
 LEFT3 = [[0, 1, 2], [1, 2, 3], [2, 3, 4]]
 RIGHT3 = [[5, 4, 3], [4, 3, 2], [3, 2, 1]]
 
@@ -234,6 +258,9 @@ RIGHT3 = [[5, 4, 3], [4, 3, 2], [3, 2, 1]]
 def edge_prep(mesh, topo, e, opts):
     """All geometry-only data of one edge: stencil, direction and the 48 interpolation weights."""
     ids, rel, ell, n = edge_geometry(mesh, topo, e)
+    if opts.conservative:            # projection and Riemann flux along the dual-face normal
+        S = dual_faces(mesh, topo)[0][e]
+        n = S / np.sqrt(S[0] * S[0] + S[1] * S[1])
     w5L, rL = five_node_weights(rel[LEFT5], ell, near=2, sv_rtol=opts.sv_rtol)
     w5R, rR = five_node_weights(rel[RIGHT5], ell, near=2, sv_rtol=opts.sv_rtol)
     w3 = np.zeros((2, 3, 3))
@@ -283,9 +310,13 @@ def div_rows(mesh, topo, v, opts):
     te = topo["edges"][edges]
     xm = np.zeros((len(edges), 2))
     nm = np.zeros((len(edges), 2))
+    if opts.conservative:
+        Sd, Ad = dual_faces(mesh, topo)
     for k, (a, b) in enumerate(te):
         d = disp(mesh, a, b)
         xm[k] = (disp(mesh, v, a) + 0.5 * d) / ell
+        if opts.conservative:        # h is the flux along the dual-face normal
+            d = Sd[edges[k]]
         nm[k] = d / np.sqrt(d[0] * d[0] + d[1] * d[1])
     deg = opts.div_degree
     while True:
@@ -306,6 +337,15 @@ def div_rows(mesh, topo, v, opts):
     d0 = (Ap[1] + Ap[K + 2]) / ell
     dx = (Ap[3] + Ap[K + 4]) / ell ** 2
     dy = (Ap[4] + Ap[K + 5]) / ell ** 2
+    if opts.conservative:
+        # divergence of the value flux as the median-dual cell's boundary integral: the flux
+        # through face e is |S_e| h_e, leaving the tail's cell and entering the head's
+        d0 = np.zeros_like(d0)
+        N = len(verts)
+        for k, (a, b) in enumerate(te):
+            if v in (a, b):
+                sgn = 1.0 if v == a else -1.0
+                d0[2 * N + k] = sgn * np.linalg.norm(Sd[edges[k]]) / Ad[v]
     return verts, edges, np.stack([d0, dx, dy]), deg
 
 

@@ -404,7 +404,8 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
   }
   if (o->div_degree < 2 || o->div_degree > 6 || o->visc_degree < 2 || o->visc_degree > 6 ||
       o->precision < 0 || o->precision > 1 || !(o->visc_coef_max > 0.0) ||
-      (o->dev_alloc == nullptr) != (o->dev_free == nullptr) || o->flux < 0 || o->flux > 1) {
+      (o->dev_alloc == nullptr) != (o->dev_free == nullptr) || o->flux < 0 || o->flux > 1 ||
+      o->conservative < 0 || o->conservative > 1) {
     set_error("hfd_prep_create: option out of range");
     return HFD_ERR_ARG;
   }
@@ -523,6 +524,35 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
     }
     P->lmin[v] = m;
   }
+  if (o->conservative) {
+    // median-dual geometry: per triangle, the segment from each edge's midpoint to the
+    // centroid, turned by 90 degrees and oriented tail -> head, adds to that edge's dual face;
+    // a third of the triangle's area goes to each corner's cell (triangle order, as a reference
+    // evaluation would sum them)
+    P->dual_S.assign(2 * E, 0.0);
+    P->dual_A.assign(nv, 0.0);
+    for (int t = 0; t < d->ntri; ++t) {
+      const int* tv = &P->tri[3 * (size_t)t];
+      double x[3][2] = {{0.0, 0.0},
+                        {P->dispx(tv[0], tv[1]), P->dispy(tv[0], tv[1])},
+                        {P->dispx(tv[0], tv[2]), P->dispy(tv[0], tv[2])}};
+      double gx = (x[0][0] + x[1][0] + x[2][0]) / 3.0, gy = (x[0][1] + x[1][1] + x[2][1]) / 3.0;
+      static const int pr[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+      for (int k = 0; k < 3; ++k) {
+        int i = pr[k][0], j = pr[k][1];
+        int ia = tv[i] < tv[j] ? i : j, ib = ia == i ? j : i;
+        double sx = gx - 0.5 * (x[i][0] + x[j][0]), sy = gy - 0.5 * (x[i][1] + x[j][1]);
+        double nx = sy, ny = -sx;
+        if (nx * (x[ib][0] - x[ia][0]) + ny * (x[ib][1] - x[ia][1]) < 0) { nx = -nx; ny = -ny; }
+        uint64_t key = ((uint64_t)tv[ia] << 32) | (uint32_t)tv[ib];
+        int64_t e = std::lower_bound(keys.begin(), keys.end(), key) - keys.begin();
+        P->dual_S[2 * e] += nx;
+        P->dual_S[2 * e + 1] += ny;
+      }
+      double area = 0.5 * (x[1][0] * x[2][1] - x[1][1] * x[2][0]);
+      for (int k = 0; k < 3; ++k) P->dual_A[tv[k]] += area / 3.0;
+    }
+  }
   int nthreads = o->nthreads > 0 ? o->nthreads : (int)std::max(1u, std::thread::hardware_concurrency());
 
   // ---- two-level stencils of active vertices (Fig. 6: distance <= 2, edges inside the set)
@@ -604,6 +634,10 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
       double ex = P->dispx(a, b), ey = P->dispy(a, b);
       xm[2 * j] = (P->dispx(v, a) + 0.5 * ex) / ell;
       xm[2 * j + 1] = (P->dispy(v, a) + 0.5 * ey) / ell;
+      if (o->conservative) {                 // h is the flux along the dual-face normal
+        ex = P->dual_S[2 * (size_t)eds[j]];
+        ey = P->dual_S[2 * (size_t)eds[j] + 1];
+      }
       double len = std::sqrt(ex * ex + ey * ey);
       nm[2 * j] = ex / len;
       nm[2 * j + 1] = ey / len;
@@ -642,6 +676,18 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
       c[i] = out[i] / ell;
       c[rows + i] = out[rows + i] / (ell * ell);
       c[2 * rows + i] = out[2 * rows + i] / (ell * ell);
+    }
+    if (o->conservative) {
+      // the value rows as the median-dual cell's boundary integral: the flux through face e,
+      // |S_e| h_e, leaves the tail's cell and enters the head's
+      for (int i = 0; i < rows; ++i) c[i] = 0.0;
+      for (int j = 0; j < M; ++j) {
+        int a = P->edges[2 * eds[j]], b = P->edges[2 * eds[j] + 1];
+        if (a != v && b != v) continue;
+        double sx = P->dual_S[2 * (size_t)eds[j]], sy = P->dual_S[2 * (size_t)eds[j] + 1];
+        double mag = std::sqrt(sx * sx + sy * sy);
+        c[2 * N + j] = (a == v ? 1.0 : -1.0) * mag / P->dual_A[v];
+      }
     }
     if (o->viscous) {                       // vertex-only LS, f and g decoupled (Sec. 2.3)
       // Degree visc_degree, dropping by one while a weight of the rows used (first and second
@@ -737,6 +783,12 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
       for (int k = 0; k < 6; ++k) P->stencil[6 * f + k] = ids[k];
       P->normal[2 * f] = dabx / ell;
       P->normal[2 * f + 1] = daby / ell;
+      if (o->conservative) {             // projection and Riemann flux along the dual normal
+        double sx = P->dual_S[2 * (size_t)e], sy = P->dual_S[2 * (size_t)e + 1];
+        double sl = std::sqrt(sx * sx + sy * sy);
+        P->normal[2 * f] = sx / sl;
+        P->normal[2 * f + 1] = sy / sl;
+      }
       int rl = five_node(&rel[0], ell, o->sv_rtol, &P->w5[30 * f]);
       int rr = five_node(&rel[1], ell, o->sv_rtol, &P->w5[30 * f + 15]);
       if (rl == 0 || rr == 0) {
@@ -854,6 +906,8 @@ Arr lookup(const Prep* P, const char* name) {
   if (s == "visc_coef") return D(P->visc_coef, true);
   if (s == "visc_degree") return I(P->visc_degree);
   if (s == "lmin") return D(P->lmin, false);
+  if (s == "dual_S") return D(P->dual_S, false);
+  if (s == "dual_A") return D(P->dual_A, false);
   return Arr{nullptr, -1, 0, false};
 }
 }  // namespace
@@ -868,7 +922,8 @@ hfd_status hfd_prep_concat(const hfd_prep* const* preps, int32_t n, hfd_prep** o
     if (o.viscous != o0.viscous || o.gamma != o0.gamma || o.mu != o0.mu || o.prandtl != o0.prandtl ||
         o.R_gas != o0.R_gas || o.weno_eps != o0.weno_eps || o.sens_lo != o0.sens_lo ||
         o.sens_hi != o0.sens_hi || o.harten != o0.harten || o.cfl != o0.cfl ||
-        o.precision != o0.precision || o.visc_coef_max != o0.visc_coef_max || o.flux != o0.flux) {
+        o.precision != o0.precision || o.visc_coef_max != o0.visc_coef_max || o.flux != o0.flux ||
+        o.conservative != o0.conservative) {
       hfd::set_error("hfd_prep_concat: member %d has different physical/numerical options", k);
       return HFD_ERR_ARG;
     }

@@ -40,6 +40,9 @@ struct Prep {
   std::vector<double> w3;                      // 18*Ef: side, sub-stencil, node
   std::vector<int32_t> rank;                   // 2*Ef
   std::vector<double> lmin;                    // nv: shortest incident edge (time step)
+  // conservative variant: dual-face area vectors (2*E, oriented tail -> head) and median-dual
+  // cell areas (nv)
+  std::vector<double> dual_S, dual_A;
   // batches (hfd_prep_concat): member mesh of each vertex and each member's bounding box
   // (x0, x1, y0, y1) for the space-filling-curve keys; empty / 1 for a single mesh
   std::vector<int32_t> member;

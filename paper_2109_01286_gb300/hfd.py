@@ -70,7 +70,8 @@ class Options(ctypes.Structure):
                 ("sv_rtol", ctypes.c_double), ("div_cond_min", ctypes.c_double),
                 ("harten", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("visc_coef_max", ctypes.c_double), ("dev_alloc", _ALLOC_FN),
-                ("dev_free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("flux", ctypes.c_int32)]
+                ("dev_free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("flux", ctypes.c_int32),
+                ("conservative", ctypes.c_int32)]
 
 
 class MeshDesc(ctypes.Structure):

@@ -413,3 +413,35 @@ def test_tiny_periodic_mesh_kernel_parity(n):
     assert len(keep) > 0.8 * len(P.active)
     err = rel_l2_groups(R, R_ref, keep)
     assert max(err) < TOL_FP64, err
+
+
+@pytest.mark.parametrize("case", ["c1", "quad"])
+def test_conservative_variant_kernel_parity(case, request):
+    """hfd_options.conservative = 1 (median-dual value rows, dual-normal fluxes) against the
+    oracle's conservative variant, FP64 kernel parity."""
+    pkg = _hfd()
+    m = request.getfixturevalue(case)[0]
+    U = request.getfixturevalue(case)[2]
+    opts = oracle.Options(conservative=True)
+    P = oracle.prepare(m, opts)
+    mesh = _kernel_mesh(pkg, m, P, conservative=True)
+    R = _residual(mesh, U)
+    R_ref = oracle.residual(m, P, U.copy(), opts)
+    keep = np.setdiff1d(P.active, near_threshold_vertices(m, P, U, opts))
+    assert len(keep) > 0.95 * len(P.active)
+    err = rel_l2_groups(R, R_ref, keep)
+    assert max(err) < TOL_FP64, err
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_conservative_variant_conserves_on_the_gpu(c1, precision, tol):
+    """The library's own coefficients: on the periodic vortex mesh sum_v |C_v| R_v vanishes for
+    the conserved rows, relative to sum_v |C_v| |R_v|, in FP64 and in FP32 bulk."""
+    pkg = _hfd()
+    m, _, U = c1
+    prep = pkg.Prep(m, conservative=True)
+    A = prep.get("dual_A")
+    R = _residual(prep.upload(precision), U)
+    total = (R[:4] * A).sum(axis=1)
+    scale = (np.abs(R[:4]) * A).sum(axis=1)
+    assert np.all(np.abs(total) < tol * scale), (total, scale)

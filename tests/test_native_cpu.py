@@ -103,6 +103,26 @@ def test_host_prep_viscous_degree_drop_matches_oracle(pkg):
     assert np.abs(prep.get("visc_coef") - ref).max() < 1e-10 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("kind", ["periodic", "ghosts"])
+def test_host_prep_conservative_matches_oracle(pkg, kind):
+    """Conservative variant: dual faces, cell areas and flux directions bit-identical to the
+    oracle's; divergence rows (finite-volume value rows, least-squares derivative rows with
+    dual-normal edge rows) to rounding."""
+    from gpu_helpers import oracle_blocks
+    if kind == "periodic":
+        m = synth.jittered_grid(16, 16, 1.0, 1.0, seed=3)
+    else:
+        m = synth.jittered_box_with_ghosts(12, 10, (0.0, 1.0), (0.0, 1.0), 5, seed=2)
+    P = oracle.prepare(m, oracle.Options(conservative=True))
+    prep = pkg.Prep(m, conservative=True)
+    S, A = oracle.hfd_oracle.dual_faces(m, P.topo)
+    np.testing.assert_array_equal(prep.get("dual_S").reshape(-1, 2), S)
+    np.testing.assert_array_equal(prep.get("dual_A"), A)
+    np.testing.assert_array_equal(prep.get("normal").reshape(-1, 2), P.normal)
+    ref = oracle_blocks(P, len(m["x"]))["div_coef"]
+    assert np.abs(prep.get("div_coef") - ref).max() < 1e-12 * np.abs(ref).max()
+
+
 def test_host_prep_with_ghosts_matches_oracle(pkg):
     m = synth.jittered_box_with_ghosts(20, 16, (0.0, 1.0), (0.0, 1.0), 5, seed=2)
     P = oracle.prepare(m)
