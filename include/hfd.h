@@ -58,7 +58,9 @@ typedef struct {
   int32_t periodic_y;
   int32_t nghost;          /* transmissive ghost vertices (no residual, refreshed by copy)  */
   const int32_t* ghost_ids;    /* nghost ids                                                */
-  const int32_t* ghost_donor;  /* nghost donor ids (non-ghost vertices)                     */
+  const int32_t* ghost_donor;  /* nghost donor ids (non-ghost vertices), or -1: a fixed ghost
+                                  (a wall band, Sec. 3.2) whose 12 values the caller sets in
+                                  the state and no refresh changes                          */
   const int32_t* ghost_flags;  /* bit 0: zero w_x on refresh, bit 1: zero w_y               */
 } hfd_mesh_desc;
 

@@ -22,10 +22,12 @@ def _ghost_transpose(mesh, g):
     """Adjoint of the ghost refresh: ghost columns pass their (masked) sensitivities to their
     donors and become zero."""
     gid = np.asarray(mesh["ghost_ids"], dtype=np.int64)
-    if len(gid) == 0:
-        return g
     dn = np.asarray(mesh["ghost_donor"], dtype=np.int64)
     fl = np.asarray(mesh["ghost_flags"])
+    g[:, gid[dn < 0]] = 0.0                    # fixed ghosts: given values, no dependence
+    gid, dn, fl = gid[dn >= 0], dn[dn >= 0], fl[dn >= 0]
+    if len(gid) == 0:
+        return g
     gg = g[:, gid].copy()
     gg[4:8, (fl & 1) != 0] = 0.0
     gg[8:12, (fl & 2) != 0] = 0.0

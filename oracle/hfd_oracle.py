@@ -578,12 +578,15 @@ def riemann_flux(wl, wr, nx, ny, opts):
 
 def ghost_fill(mesh, U):
     """Transmissive ghost refresh (R14): copy the donor's 12 values, zero the derivative normal
-    to the boundary (flag bit 0: x, bit 1: y).  In place; returns U."""
+    to the boundary (flag bit 0: x, bit 1: y).  Ghosts with donor -1 are fixed (R22: wall bands
+    holding given values) and keep theirs.  In place; returns U."""
     g = np.asarray(mesh["ghost_ids"], dtype=np.int64)
-    if len(g) == 0:
-        return U
     d = np.asarray(mesh["ghost_donor"], dtype=np.int64)
     f = np.asarray(mesh["ghost_flags"])
+    keep = d >= 0
+    g, d, f = g[keep], d[keep], f[keep]
+    if len(g) == 0:
+        return U
     U[:, g] = U[:, d]
     U[4:8, g[(f & 1) != 0]] = 0.0
     U[8:12, g[(f & 2) != 0]] = 0.0

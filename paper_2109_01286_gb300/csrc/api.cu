@@ -264,7 +264,7 @@ hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
   std::vector<int32_t> gid(d.G), gdn(d.G), gfl(d.G);
   for (int g = 0; g < d.G; ++g) {
     gid[g] = inv[P.ghost_ids[g]];
-    gdn[g] = inv[P.ghost_donor[g]];
+    gdn[g] = P.ghost_donor[g] < 0 ? -1 : inv[P.ghost_donor[g]];   // -1: fixed ghost
     gfl[g] = P.ghost_flags[g];
   }
   TRY(dev_upload(m, (void**)&d.gid, gid));
@@ -328,7 +328,7 @@ hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
 }
 
 hfd_status residual_impl(hfd_mesh* m, double* U, double* R, cudaStream_t s) {
-  CK(hfd::launch_ghost(m->dm, U, s));
+  CK(hfd::launch_ghost(m->dm, U, U, s));
   CK(hfd::launch_vertex(m->dm, U, m->ph, s));
   CK(hfd::launch_edge(m->dm, m->ph, s));
   CK(hfd::launch_div(m->dm, U, U, R, hfd::DIV_RESIDUAL, 0.0, 1.0, 1.0, m->ph, m->lanes, s));
@@ -385,7 +385,7 @@ hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* t
       }));
       continue;
     }
-    if (d.G) CK(timed(0, [&] { return hfd::launch_ghost(d, in[k], s); }));
+    if (d.G) CK(timed(0, [&] { return hfd::launch_ghost(d, in[k], U, s); }));
     CK(timed(1, [&] { return hfd::launch_vertex(d, in[k], m->ph, s); }));
     CK(timed(2, [&] { return hfd::launch_edge(d, m->ph, s); }));
     CK(timed(3, [&] {
@@ -393,7 +393,7 @@ hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* t
                              m->lanes, s);
     }));
   }
-  if (d.G) CK(timed(0, [&] { return hfd::launch_ghost(d, U, s); }));
+  if (d.G) CK(timed(0, [&] { return hfd::launch_ghost(d, U, U, s); }));
   return HFD_OK;
 }
 
@@ -612,7 +612,7 @@ hfd_status hfd_mesh_autotune(hfd_mesh* m, const double* U, void* stream, int32_t
         CK(hfd::launch_stage_persistent(d, m->U1, m->U1, m->U2, hfd::DIV_STAGE, 0.0, 1.0, dt,
                                         m->ph, m->lanes, c.grid, true, s));
       } else {
-        if (d.G) CK(hfd::launch_ghost(d, m->U1, s));
+        if (d.G) CK(hfd::launch_ghost(d, m->U1, m->U1, s));
         CK(hfd::launch_vertex(d, m->U1, m->ph, s));
         CK(hfd::launch_edge(d, m->ph, s));
         CK(hfd::launch_div(d, m->U1, m->U1, m->U2, hfd::DIV_STAGE, 0.0, 1.0, dt, m->ph, m->lanes, s));

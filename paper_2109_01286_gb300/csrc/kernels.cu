@@ -749,10 +749,20 @@ __global__ void __launch_bounds__(256, DivOcc<T>::kMinBlocks) k_div(int A, int V
 }
 
 // ------------------------------------------------------------------ small kernels
+// Ghost refresh of state U (R14): a transmissive ghost copies its donor in U and zeroes the
+// derivative normal to its boundary; a fixed ghost (donor -1, wall bands holding given values)
+// takes its values from the step's base state `base` (nothing to do when U is the base).
 __device__ __forceinline__ void ghost_body(int g, int Gn, int V, const int32_t* gid,
-                                           const int32_t* gdonor, const int32_t* gflags, double* U) {
+                                           const int32_t* gdonor, const int32_t* gflags, double* U,
+                                           const double* base) {
   if (g >= Gn) return;
   int t = gid[g], d = gdonor[g], f = gflags[g];
+  if (d < 0) {
+    if (base != U)
+#pragma unroll
+      for (int r = 0; r < 12; ++r) U[(size_t)r * V + t] = base[(size_t)r * V + t];
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < 12; ++r) {
     double val = U[(size_t)r * V + d];
@@ -762,8 +772,8 @@ __device__ __forceinline__ void ghost_body(int g, int Gn, int V, const int32_t* 
 }
 
 __global__ void k_ghost(int Gn, int V, const int32_t* gid, const int32_t* gdonor,
-                        const int32_t* gflags, double* U) {
-  ghost_body(blockIdx.x * blockDim.x + threadIdx.x, Gn, V, gid, gdonor, gflags, U);
+                        const int32_t* gflags, double* U, const double* base) {
+  ghost_body(blockIdx.x * blockDim.x + threadIdx.x, Gn, V, gid, gdonor, gflags, U, base);
 }
 
 // min over the active vertices of each mesh of l_min / (|u| + c) (R12), in two passes without
@@ -907,7 +917,7 @@ __global__ void __launch_bounds__(128) k_stage(KernelArgs ka, StageArgs sa, Phys
   double* U = const_cast<double*>(sa.Us);
   if (do_ghost) {
     for (int g = tid; g < ka.G; g += stride)
-      ghost_body(g, ka.G, ka.V, ka.gid, ka.gdonor, ka.gflags, U);
+      ghost_body(g, ka.G, ka.V, ka.gid, ka.gdonor, ka.gflags, U, sa.Un);
     if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
   }
   for (int v = tid; v < ka.V; v += stride)
@@ -941,9 +951,9 @@ KernelArgs kernel_args(const DevMesh& m) {
   return a;
 }
 
-cudaError_t launch_ghost(const DevMesh& m, double* U, cudaStream_t s) {
+cudaError_t launch_ghost(const DevMesh& m, double* U, const double* base, cudaStream_t s) {
   if (m.G == 0) return cudaSuccess;
-  k_ghost<<<blocks(m.G, 256), 256, 0, s>>>(m.G, m.V, m.gid, m.gdonor, m.gflags, U);
+  k_ghost<<<blocks(m.G, 256), 256, 0, s>>>(m.G, m.V, m.gid, m.gdonor, m.gflags, U, base);
   return cudaGetLastError();
 }
 

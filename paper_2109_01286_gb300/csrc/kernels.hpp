@@ -99,7 +99,9 @@ struct KernelArgs {
   unsigned spins;
 };
 
-cudaError_t launch_ghost(const DevMesh& m, double* U, cudaStream_t s);
+// Ghost refresh of U; fixed ghosts (donor -1) take their values from `base` (the step's input
+// state; pass U itself outside a step).
+cudaError_t launch_ghost(const DevMesh& m, double* U, const double* base, cudaStream_t s);
 cudaError_t launch_vertex(const DevMesh& m, const double* U, const Phys& ph, cudaStream_t s);
 cudaError_t launch_edge(const DevMesh& m, const Phys& ph, cudaStream_t s);
 // out = R (residual mode) or out = a*Un + b*(Us + dt*R) (stage mode); dt_fixed <= 0 selects

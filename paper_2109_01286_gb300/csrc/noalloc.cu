@@ -95,7 +95,7 @@ extern "C" hfd_status hfd_residual_static(hfd_mesh* m, double* U, double* R, voi
   d.FGv = src.viscous ? p + b_ua + b_fg : nullptr;
   d.h = p + b_ua + b_fg + b_fgv;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = hfd::launch_ghost(d, U, s);
+  cudaError_t e = hfd::launch_ghost(d, U, U, s);
   if (e == cudaSuccess) e = hfd::launch_vertex(d, U, m->ph, s);
   if (e == cudaSuccess) e = hfd::launch_edge(d, m->ph, s);
   if (e == cudaSuccess)

@@ -442,8 +442,9 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
     }
     for (int g = 0; g < d->nghost; ++g) {
       int dn = d->ghost_donor[g];
+      if (dn == -1) continue;              // fixed ghost: the caller's values are kept
       if (dn < 0 || dn >= nv || P->is_ghost[dn]) {
-        set_error("hfd_prep_create: ghost donor %d invalid (must be a non-ghost vertex)", dn);
+        set_error("hfd_prep_create: ghost donor %d invalid (must be a non-ghost vertex or -1)", dn);
         return HFD_ERR_MESH;
       }
     }
@@ -943,7 +944,7 @@ hfd_status hfd_prep_concat(const hfd_prep* const* preps, int32_t n, hfd_prep** o
     B->y.insert(B->y.end(), P.y.begin(), P.y.end());
     addv(B->tri, P.tri, vo);
     addv(B->ghost_ids, P.ghost_ids, vo);
-    addv(B->ghost_donor, P.ghost_donor, vo);
+    for (int32_t dn : P.ghost_donor) B->ghost_donor.push_back(dn < 0 ? dn : dn + vo);
     B->ghost_flags.insert(B->ghost_flags.end(), P.ghost_flags.begin(), P.ghost_flags.end());
     B->is_ghost.insert(B->is_ghost.end(), P.is_ghost.begin(), P.is_ghost.end());
     addv(B->edges, P.edges, vo);

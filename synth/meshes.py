@@ -12,7 +12,8 @@ Two kinds of axis are supported:
               names a donor (the nearest physical vertex, by clamping the grid index) and flags
               which derivative components are zeroed when it is refreshed (bit 0: the x
               derivatives, bit 1: the y derivatives, i.e. the derivative normal to the boundary
-              the ghost lies beyond).
+              the ghost lies beyond).  A donor of -1 marks a fixed ghost, whose values the
+              caller sets and nothing refreshes (`couette_channel`).
 
 Vertex ids are row-major over the (possibly ghost-extended) grid.  Random draws, in order from
 numpy's PCG64(seed): x jitter for all vertices, y jitter for all vertices, one diagonal bit
@@ -89,6 +90,16 @@ def jittered_box_with_ghosts(nx, ny, xr, yr, ghost, seed, jitter=0.15, periodic_
     """nx-by-ny physical vertices on the closed box xr x yr with `ghost` ghost layers outside
     each bounded side (y may instead be periodic).  Boundary lines and ghosts are unjittered."""
     return _grid(nx, ny, xr, yr, False, periodic_y, ghost, jitter, seed)
+
+
+def couette_channel(nx, ny, ghost, seed, jitter=0.15, half=5.0):
+    """Channel of Sec. 3.2: x periodic on [-half, half), walls at y = -half and y = +half,
+    `ghost` layers of fixed ghost vertices beyond each wall (donor -1: the caller's values are
+    kept, here the exact solution).  nx-by-ny physical vertices."""
+    m = _grid(nx, ny, (-half, half), (-half, half), True, False, ghost, jitter, seed)
+    m["ghost_donor"] = np.full(len(m["ghost_ids"]), -1, dtype=np.int32)
+    m["ghost_flags"] = np.zeros(len(m["ghost_ids"]), dtype=np.int32)
+    return m
 
 
 def mesh_summary(mesh):

@@ -90,3 +90,22 @@ def taylor_green(mesh, mach=0.1, gamma=GAMMA):
                 p0 + 0.25 * (np.cos(2 * x) + np.cos(2 * y)))
 
     return _state_from_prim_fn(mesh["x"], mesh["y"], prim, gamma)
+
+
+def couette(mesh, u0=1.0, T_bottom=10.0, T_top=12.0, p=10.0, gamma=GAMMA, cp=10.0, kappa=0.01,
+            mu=0.1, half=5.0):
+    """Exact compressible Couette flow of Sec. 3.2 between walls at y = -half (moving at -u0)
+    and y = +half (+u0): u = u0 y / half, v = 0, uniform p, and the temperature that balances
+    conduction against viscous heating, kappa T'' + mu u'^2 = 0, with T = T_bottom / T_top at
+    the walls; rho = gamma p / ((gamma - 1) cp T).  Extended unchanged into the ghost bands."""
+    L = 2.0 * half
+
+    def prim(x, y):
+        u = 2.0 * y / L * u0
+        T = (-2.0 * mu * u0 * u0 / (kappa * L * L) * y * y + (T_top - T_bottom) / L * y
+             + 0.5 * (T_top + T_bottom) + 0.5 * mu * u0 * u0 / kappa)
+        rho = gamma * p / ((gamma - 1.0) * cp * T)
+        return rho, u, 0.0 * y, p + 0.0 * y
+
+    return _state_from_prim_fn(mesh["x"], mesh["y"], prim, gamma)
+

@@ -445,3 +445,35 @@ def test_conservative_variant_conserves_on_the_gpu(c1, precision, tol):
     total = (R[:4] * A).sum(axis=1)
     scale = (np.abs(R[:4]) * A).sum(axis=1)
     assert np.all(np.abs(total) < tol * scale), (total, scale)
+
+
+def test_couette_channel_with_wall_bands_kernel_parity():
+    """Sec. 3.2 Couette channel: x periodic, fixed ghost bands beyond both walls (donor -1)
+    holding the exact solution, viscous (the paper's c_p = 10, kappa = 1/100, mu = 1/10).
+    Residual and three SSP-RK3 steps through the graph path against the oracle (kernel parity);
+    the ghost bands keep their values through the steps (every stage refreshes them from the
+    step's input state)."""
+    pkg = _hfd()
+    R_gas = 0.4 * 10.0 / 1.4
+    m = synth.couette_channel(16, 17, 6, seed=7)
+    U = synth.couette(m)
+    kw = dict(viscous=True, mu=0.1, prandtl=100.0, R_gas=R_gas)
+    opts = oracle.Options(**kw)
+    P = oracle.prepare(m, opts)
+    mesh = _kernel_mesh(pkg, m, P, **kw)
+    R = _residual(mesh, U)
+    R_ref = oracle.residual(m, P, U.copy(), opts)
+    scale = np.abs(oracle.euler_flux(U[:4], 1.4)[0]).max() / (10.0 / 16)
+    assert np.abs(R - R_ref).max() < 1e-12 * scale
+    dt = 0.2 * oracle.cfl_dt(m, P, U)
+    X = mesh.import_state(torch.from_numpy(U).cuda())
+    ref = U.copy()
+    for _ in range(3):
+        ref = oracle.step(m, P, ref, dt, opts)
+        mesh.steps(X, dt, 1)
+    out = mesh.export_state(X).cpu().numpy()
+    # near the steady state the increments are tiny: compare the states to rounding
+    for rows in (slice(0, 4), slice(4, 12)):
+        assert np.abs(out[rows] - ref[rows]).max() <= 1e-13 * np.abs(U[rows]).max()
+    g = m["ghost_ids"]
+    np.testing.assert_array_equal(out[:, g], U[:, g])

@@ -563,6 +563,30 @@ def test_conservative_variant_truncation_order():
     assert orders.min() > 1.5, (errs, orders)
 
 
+def test_couette_viscous_divergence_vanishes_with_wall_bands():
+    """Sec. 3.2: in compressible Couette flow the viscous fluxes are linear in y (tau_xy = mu
+    u', u tau_xy + kappa T' with kappa T'' = -mu u'^2), so the degree-4 viscous rows must return
+    div f_vis = 0, and 0 for its x/y derivatives, to rounding at every active vertex, including
+    the rows next to the walls that read the fixed ghost bands (R22).  kappa = mu c_p / Pr with
+    the paper's c_p = 10, kappa = 1/100, mu = 1/10 (Pr = 100, R = (gamma-1) c_p / gamma); a
+    wrong heat-flux or stress constant breaks the energy balance."""
+    R_gas = 0.4 * 10.0 / 1.4
+    m = synth.couette_channel(12, 13, 6, seed=7)
+    U = synth.couette(m)
+    visc = oracle.Options(viscous=True, mu=0.1, prandtl=100.0, R_gas=R_gas)
+    inv = oracle.Options()
+    P = oracle.prepare(m, visc)
+    Rv = oracle.residual(m, P, U.copy(), visc) - oracle.residual(m, P, U.copy(), inv)
+    Fv, Gv = oracle.viscous_flux(U, visc)
+    scale = np.abs(Gv).max() / (10.0 / 12)
+    assert np.abs(Rv[:, P.active]).max() < 1e-11 * scale
+    assert np.abs(Gv[3]).max() > 1e-3                   # the heat and work fluxes are not zero
+    # the ghost bands keep their values through a step
+    U1 = oracle.step(m, P, U.copy(), 1e-3, visc)
+    g = m["ghost_ids"]
+    np.testing.assert_array_equal(U1[:, g], U[:, g])
+
+
 def test_ssp_rk3_is_third_order():
     lam = -1.3 + 0.4j
     errs = []
