@@ -164,6 +164,25 @@ hfd_status hfd_prep_set(hfd_prep* prep, const char* name, const void* src, int64
  * n values.  The inputs are not consumed.  Errors: HFD_ERR_ARG. */
 hfd_status hfd_prep_concat(const hfd_prep* const* preps, int32_t n, hfd_prep** out);
 
+/* ---------------------------------------------------------------- batches, one array per member
+ * The batch form of Sec. 3's test problems, with one state array per member mesh (the
+ * concatenated form is hfd_prep_concat + hfd_mesh_upload, whose single state holds all members).
+ * hfd_batch_create: the disjoint union of n preps uploaded in `precision` (-1 / 0 / 1 as in
+ * hfd_mesh_upload).  hfd_batch_step advances every member by one SSP-RK3 step (Sec. 2.3, end)
+ * in one pass of the kernels: U[k] is member k's 12 x nv_k device state in its own input order
+ * (updated in place); dt is n positive steps (host array), or NULL for each member's own CFL
+ * step.  It gathers the members into the batch's array, steps it, scatters the result back,
+ * and returns after the stream has finished (the host arrays U and dt may then be reused).
+ * hfd_batch_mesh lends the union mesh (owned by the batch) for the other hfd_mesh calls, e.g.
+ * hfd_last_dt.  Errors: HFD_ERR_ARG, HFD_ERR_CUDA, and those of hfd_prep_concat and
+ * hfd_mesh_upload. */
+typedef struct hfd_batch hfd_batch;
+hfd_status hfd_batch_create(const hfd_prep* const* preps, int32_t n, int32_t precision,
+                            hfd_batch** out);
+void hfd_batch_destroy(hfd_batch* batch);
+hfd_status hfd_batch_mesh(hfd_batch* batch, hfd_mesh** mesh);
+hfd_status hfd_batch_step(hfd_batch* batch, double* const* U, const double* dt, void* stream);
+
 /* ---------------------------------------------------------------- device mesh
  * hfd_mesh_create = hfd_prep_create + hfd_mesh_upload.  hfd_mesh_upload renumbers vertices
  * and edges (Hilbert order of coordinates; non-ghost vertices first) and uploads the

@@ -349,7 +349,10 @@ struct Timer {
 
 // One SSP-RK3 step: three stages of (ghost refresh, vertex fluxes, edge fluxes, divergence +
 // stage combination), plus the device time step and a final ghost refresh.
-hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* tm = nullptr) {
+// One SSP-RK3 step of U.  dt > 0: that step; else dt_member (device array, one step per batch
+// member) when given; else each member's CFL step.
+hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* tm = nullptr,
+                     const double* dt_member = nullptr) {
   const DevMesh& d = m->dm;
   auto timed = [&](int kind, auto&& launch) -> cudaError_t {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -366,7 +369,7 @@ hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* t
     }
     return e;
   };
-  if (!(dt > 0.0)) CK(timed(4, [&] { return hfd::launch_dtmin(d, U, m->ph, s); }));
+  if (!(dt > 0.0) && !dt_member) CK(timed(4, [&] { return hfd::launch_dtmin(d, U, m->ph, s); }));
   static const double A_[3] = {0.0, 0.75, 1.0 / 3.0}, B_[3] = {1.0, 0.25, 2.0 / 3.0};
   double* in[3] = {U, m->U1, m->U2};
   double* out[3] = {m->U1, m->U2, U};
@@ -381,7 +384,7 @@ hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* t
       CK(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
       CK(timed(5, [&] {
         return hfd::launch_stage_persistent(d, in[k], U, out[k], hfd::DIV_STAGE, A_[k], B_[k], dt,
-                                            m->ph, m->lanes, grid, true, s);
+                                            m->ph, m->lanes, grid, true, s, dt_member);
       }));
       continue;
     }
@@ -390,7 +393,7 @@ hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* t
     CK(timed(2, [&] { return hfd::launch_edge(d, m->ph, s); }));
     CK(timed(3, [&] {
       return hfd::launch_div(d, in[k], U, out[k], hfd::DIV_STAGE, A_[k], B_[k], dt, m->ph,
-                             m->lanes, s);
+                             m->lanes, s, dt_member);
     }));
   }
   if (d.G) CK(timed(0, [&] { return hfd::launch_ghost(d, U, U, s); }));
@@ -660,3 +663,87 @@ hfd_status hfd_check(hfd_mesh* m, void* stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- batches with one array per member
+struct hfd_batch {
+  hfd_mesh* mesh = nullptr;
+  int n = 0;
+  std::vector<int64_t> off;          // members' first vertex in the batch's input order
+  int64_t* d_off = nullptr;
+  double** d_ptrs = nullptr;         // the members' arrays of the current call
+  double* d_dt = nullptr;            // the members' steps of the current call
+  double* Ubat = nullptr;            // 12 x V, input order
+  double* Uint = nullptr;            // 12 x V, internal order
+};
+
+extern "C" hfd_status hfd_batch_create(const hfd_prep* const* preps, int32_t n, int32_t precision,
+                                       hfd_batch** out) {
+  if (!preps || n <= 0 || !out) { set_error("hfd_batch_create: invalid argument"); return HFD_ERR_ARG; }
+  *out = nullptr;
+  hfd_prep* cat = nullptr;
+  hfd_status st = hfd_prep_concat(preps, n, &cat);
+  if (st != HFD_OK) return st;
+  hfd_batch* b = new (std::nothrow) hfd_batch();
+  if (!b) { hfd_prep_destroy(cat); set_error("hfd_batch_create: out of host memory"); return HFD_ERR_ARG; }
+  st = hfd_mesh_upload(cat, precision, &b->mesh);
+  hfd_prep_destroy(cat);
+  if (st != HFD_OK) { delete b; return st; }
+  b->n = n;
+  b->off.assign(n + 1, 0);
+  for (int k = 0; k < n; ++k) b->off[k + 1] = b->off[k] + preps[k]->nv;
+  hfd_mesh* m = b->mesh;
+  const size_t bytes = (size_t)12 * m->dm.V * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = mesh_malloc(m, (void**)&b->d_off, sizeof(int64_t) * (n + 1));
+  if (e == cudaSuccess) e = mesh_malloc(m, (void**)&b->d_ptrs, sizeof(double*) * n);
+  if (e == cudaSuccess) e = mesh_malloc(m, (void**)&b->d_dt, sizeof(double) * n);
+  if (e == cudaSuccess) e = mesh_malloc(m, (void**)&b->Ubat, bytes);
+  if (e == cudaSuccess) e = mesh_malloc(m, (void**)&b->Uint, bytes);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_off, b->off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_error("hfd_batch_create: %s", cudaGetErrorString(e));
+    hfd_batch_destroy(b);
+    return HFD_ERR_CUDA;
+  }
+  *out = b;
+  return HFD_OK;
+}
+
+extern "C" void hfd_batch_destroy(hfd_batch* b) {
+  if (!b) return;
+  hfd_mesh_destroy(b->mesh);        // also releases the batch's blocks (mesh allocations)
+  delete b;
+}
+
+extern "C" hfd_status hfd_batch_mesh(hfd_batch* b, hfd_mesh** mesh) {
+  if (!b || !mesh) { set_error("hfd_batch_mesh: invalid argument"); return HFD_ERR_ARG; }
+  *mesh = b->mesh;
+  return HFD_OK;
+}
+
+extern "C" hfd_status hfd_batch_step(hfd_batch* b, double* const* U, const double* dt,
+                                     void* stream) {
+  if (!b || !U) { set_error("hfd_batch_step: invalid argument"); return HFD_ERR_ARG; }
+  for (int k = 0; k < b->n; ++k) {
+    if (!U[k]) { set_error("hfd_batch_step: member %d has no state", k); return HFD_ERR_ARG; }
+    if (dt && !(dt[k] > 0.0)) {
+      set_error("hfd_batch_step: member %d: dt must be positive (or pass no dt array)", k);
+      return HFD_ERR_ARG;
+    }
+  }
+  hfd_mesh* m = b->mesh;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(b->d_ptrs, U, sizeof(double*) * b->n, cudaMemcpyHostToDevice, s));
+  if (dt) CK(cudaMemcpyAsync(b->d_dt, dt, sizeof(double) * b->n, cudaMemcpyHostToDevice, s));
+  const int V = m->dm.V;
+  CK(hfd::launch_batch_copy(V, b->n, b->d_off, b->d_ptrs, b->Ubat, true, s));
+  CK(hfd::launch_permute(V, m->dperm, b->Ubat, b->Uint, true, s));
+  TRY(step_impl(m, b->Uint, 0.0, s, nullptr, dt ? b->d_dt : nullptr));
+  CK(hfd::launch_permute(V, m->dperm, b->Uint, b->Ubat, false, s));
+  CK(hfd::launch_batch_copy(V, b->n, b->d_off, b->d_ptrs, b->Ubat, false, s));
+  // the host arrays U and dt may be reused by the caller as soon as this returns
+  CK(cudaStreamSynchronize(s));
+  return HFD_OK;
+}
+

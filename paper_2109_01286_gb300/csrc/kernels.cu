@@ -513,6 +513,7 @@ struct StageArgs {
   double* out;
   int mode;
   double a, b, dt_fixed;
+  const double* dt_member;   // per-mesh step of a batch (dt_fixed <= 0), or nullptr
 };
 
 // FP32-bulk gather of one vertex's divergence rows over the chunked layout: lane `lane` of
@@ -695,7 +696,9 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
   if (!live) return;
   // time step of this vertex's mesh (a batch holds several meshes, each with its own CFL step)
   const int mem = vmem ? __ldg(vmem + r) : 0;
-  double dt = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)dtbits[mem]);
+  double dt = dt_fixed > 0.0 ? dt_fixed
+               : sa.dt_member ? __ldg(sa.dt_member + mem)
+                              : cfl * __longlong_as_double((long long)dtbits[mem]);
   if (mode == DIV_STAGE && lane == 0 && dt_last && (r == 0 || (vmem && __ldg(vmem + r - 1) != mem)))
     dt_last[mem] = dt;
   // rows held by this lane after the reduce-scatter: base .. base + per - 1
@@ -1004,9 +1007,9 @@ static void div_dispatch(const DevMesh& m, const StageArgs& sa, const Phys& ph, 
 
 cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, double* out, int mode,
                        double a, double b, double dt_fixed, const Phys& ph, int lanes,
-                       cudaStream_t s) {
+                       cudaStream_t s, const double* dt_member) {
   if (m.A == 0) return cudaSuccess;
-  StageArgs sa{Us, Un, out, mode, a, b, dt_fixed};
+  StageArgs sa{Us, Un, out, mode, a, b, dt_fixed, dt_member};
   if (m.precision == 0) {
     switch (lanes) {
       case 1: div_dispatch<double, 1>(m, sa, ph, s); break;
@@ -1051,9 +1054,9 @@ cudaError_t persistent_max_blocks(const DevMesh& m, int lanes, int* per_sm, int*
 cudaError_t launch_stage_persistent(const DevMesh& m, const double* Us, const double* Un,
                                     double* out, int mode, double a, double b, double dt_fixed,
                                     const Phys& ph, int lanes, int grid, bool do_ghost,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, const double* dt_member) {
   KernelArgs ka = kernel_args(m);
-  StageArgs sa{Us, Un, out, mode, a, b, dt_fixed};
+  StageArgs sa{Us, Un, out, mode, a, b, dt_fixed, dt_member};
   Phys p = ph;
   int dg = do_ghost && m.G > 0 ? 1 : 0;
   void* args[] = {&ka, &sa, &p, &dg};
@@ -1078,6 +1081,31 @@ cudaError_t launch_dtmin(const DevMesh& m, const double* U, const Phys& ph, cuda
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_dtmin_final<<<1, 1024, 0, s>>>(nb, m.A, m.vmem, m.dtpartial, m.dtbits);
+  return cudaGetLastError();
+}
+
+// One thread per (row, vertex) of the batch array; the member is found by binary search of
+// the offsets.
+__global__ void k_batch_copy(int V, int n, const int64_t* __restrict__ off,
+                             double* const* __restrict__ ptrs, double* __restrict__ U,
+                             int to_batch) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 12LL * V) return;
+  const int r = (int)(i / V), v = (int)(i - (long long)r * V);
+  int lo = 0, hi = n;                       // off[lo] <= v < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= v) lo = mid; else hi = mid;
+  }
+  const long long nvk = __ldg(off + lo + 1) - __ldg(off + lo);
+  double* p = ptrs[lo] + (size_t)r * nvk + (v - __ldg(off + lo));
+  if (to_batch) U[i] = *p; else *p = U[i];
+}
+
+cudaError_t launch_batch_copy(int V, int n, const int64_t* off, double* const* ptrs, double* U,
+                              bool to_batch, cudaStream_t s) {
+  if (V == 0) return cudaSuccess;
+  k_batch_copy<<<blocks(12LL * V, 256), 256, 0, s>>>(V, n, off, ptrs, U, to_batch ? 1 : 0);
   return cudaGetLastError();
 }
 

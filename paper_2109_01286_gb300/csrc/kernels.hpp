@@ -105,17 +105,23 @@ cudaError_t launch_ghost(const DevMesh& m, double* U, const double* base, cudaSt
 cudaError_t launch_vertex(const DevMesh& m, const double* U, const Phys& ph, cudaStream_t s);
 cudaError_t launch_edge(const DevMesh& m, const Phys& ph, cudaStream_t s);
 // out = R (residual mode) or out = a*Un + b*(Us + dt*R) (stage mode); dt_fixed <= 0 selects
-// dt = cfl * (device minimum).
+// dt_member[mesh] when dt_member is given (device array, one step per batch member), else
+// dt = cfl * (device minimum of the vertex's mesh).
 cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, double* out,
                        int mode, double a, double b, double dt_fixed, const Phys& ph,
-                       int lanes, cudaStream_t s);
+                       int lanes, cudaStream_t s, const double* dt_member = nullptr);
 cudaError_t launch_dtmin(const DevMesh& m, const double* U, const Phys& ph, cudaStream_t s);
 // One cooperative launch running ghost refresh (optional), vertex fluxes, edge fluxes and the
 // divergence + stage update of one RK stage, phases separated by bounded grid barriers.
 cudaError_t launch_stage_persistent(const DevMesh& m, const double* Us, const double* Un,
                                     double* out, int mode, double a, double b, double dt_fixed,
                                     const Phys& ph, int lanes, int grid, bool do_ghost,
-                                    cudaStream_t s);
+                                    cudaStream_t s, const double* dt_member = nullptr);
+// Copies between one array per batch member (ptrs[k]: 12 x nv_k, input order; off: n + 1
+// device offsets of the members in the batch's input order) and the batch's 12 x V array:
+// to_batch = true gathers the members into U, false scatters U back to them.
+cudaError_t launch_batch_copy(int V, int n, const int64_t* off, double* const* ptrs, double* U,
+                              bool to_batch, cudaStream_t s);
 cudaError_t persistent_max_blocks(const DevMesh& m, int lanes, int* per_sm, int* nsm);
 cudaError_t launch_permute(int V, const int32_t* perm, const double* src, double* dst,
                            bool gather, cudaStream_t s);

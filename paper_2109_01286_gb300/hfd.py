@@ -28,7 +28,8 @@ EXPORTED = ["hfd_default_options", "hfd_last_error", "hfd_prep_create", "hfd_pre
             "hfd_state_export", "hfd_residual", "hfd_step", "hfd_steps", "hfd_steps_host",
             "hfd_last_dt", "hfd_check", "hfd_steps_profiled", "hfd_residual_static",
             "hfd_prep_concat", "hfd_mesh_set_launch", "hfd_mesh_autotune",
-            "hfd_mesh_set_barrier_limit", "hfd_adjoint"]
+            "hfd_mesh_set_barrier_limit", "hfd_adjoint", "hfd_batch_create", "hfd_batch_destroy",
+            "hfd_batch_mesh", "hfd_batch_step"]
 
 
 class HfdError(RuntimeError):
@@ -121,6 +122,11 @@ _lib.hfd_mesh_autotune.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int32)]
 _lib.hfd_mesh_set_barrier_limit.argtypes = [_P, ctypes.c_uint32]
 _lib.hfd_adjoint.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
 _lib.hfd_step.argtypes = [_P, _P, ctypes.c_double, _P]
+_lib.hfd_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.POINTER(_P)]
+_lib.hfd_batch_destroy.argtypes = [_P]
+_lib.hfd_batch_mesh.argtypes = [_P, ctypes.POINTER(_P)]
+_lib.hfd_batch_step.argtypes = [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double), _P]
 _lib.hfd_steps.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int32, _P]
 _lib.hfd_steps_host.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_int32, _P]
 _lib.hfd_last_dt.argtypes = [_P, _P, _P]
@@ -373,3 +379,44 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Several meshes with one state array per member (hfd_batch_*): each state is a 12 x nv_k
+    float64 CUDA tensor in that member's input vertex order, updated in place by step()."""
+
+    def __init__(self, preps, precision=None):
+        arr = (_P * len(preps))(*[p._h for p in preps])
+        pr = {None: -1, "fp64": 0, "fp32": 1, "mixed": 1, 0: 0, 1: 1}[precision]
+        h = _P()
+        _ok(_lib.hfd_batch_create(arr, len(preps), pr, ctypes.byref(h)), "hfd_batch_create")
+        self._h = h
+        self.n = len(preps)
+
+    def step(self, states, dt=None, stream=None):
+        """One SSP-RK3 step of every member: dt = None (each member's CFL step) or n steps."""
+        if len(states) != self.n:
+            raise ValueError(f"{len(states)} states for {self.n} members")
+        ptrs = (ctypes.c_void_p * self.n)(*[t.data_ptr() for t in states])
+        dts = None if dt is None else (ctypes.c_double * self.n)(*[float(x) for x in dt])
+        _ok(_lib.hfd_batch_step(self._h, ptrs, dts, _stream(stream)), "hfd_batch_step")
+
+    def last_dt(self, stream=None):
+        """The members' steps of the last step()."""
+        m = _P()
+        _ok(_lib.hfd_batch_mesh(self._h, ctypes.byref(m)), "hfd_batch_mesh")
+        v = (ctypes.c_double * self.n)()
+        _ok(_lib.hfd_last_dt(m, v, _stream(stream)), "hfd_last_dt")
+        return list(v)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hfd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -110,3 +110,26 @@ def test_persistent_barrier_wait_gives_up_and_reports_timeout(members):
     m.step(b, 0.01)
     torch.cuda.synchronize()
     assert (torch.linalg.norm(a - b) / torch.linalg.norm(a)).item() < 1e-12
+
+
+@pytest.mark.parametrize("given_dt", [False, True])
+def test_batch_api_with_one_array_per_member(members, given_dt):
+    """hfd_batch_step: member states in their own input order, advanced together, equal each
+    member's own mesh bit for bit, with each member's CFL step or with given steps."""
+    pkg = _pkg()
+    preps = [pkg.Prep(x["mesh"]) for x in members]
+    batch = pkg.Batch(preps)
+    states = [torch.from_numpy(np.ascontiguousarray(x["U"])).cuda() for x in members]
+    dts = [2e-3, 3e-3, 1e-3] if given_dt else None
+    for _ in range(2):
+        batch.step(states, dts)
+    got_dt = batch.last_dt()
+    for k, x in enumerate(members):
+        single = preps[k].upload()
+        X = _state(single, x["U"])
+        for _ in range(2):
+            single.step(X, dts[k] if given_dt else 0.0)
+        np.testing.assert_array_equal(states[k].cpu().numpy(), single.export_state(X).cpu().numpy())
+        assert got_dt[k] == (dts[k] if given_dt else single.last_dt())
+    with pytest.raises(pkg.HfdError):
+        batch.step(states, [1e-3, 0.0, 1e-3])
