@@ -323,6 +323,11 @@ def run_native(args):
     kd = r["kernels"][dom]
     def traffic(name):
         return DRAM_TRAFFIC_1024.get(name) if args.n == 1024 else None
+
+    def dram(name, avg_ms):
+        # the survey's % of HBM: measured DRAM bytes per launch over the live launch time
+        t = traffic(name)
+        return (None, None) if t is None else (t / (avg_ms / 1000.0) / 1e9, t / (avg_ms / 1000.0) / 1e9 / peak_hbm)
     roof = {"kernel": f"k_{dom}<double>", "bound": "alu", "achieved": kd["tflops"],
             "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
             "frac": kd["tflops"] / (FP64_PEAK_FLOPS / 1e12), "traffic": traffic(f"k_{dom}<double>"),
@@ -330,6 +335,8 @@ def run_native(args):
             "peak_source": "derived: ncu dfma peak_sustained 2/SM/clk x 152 SMs x 2 flop x 2.07 GHz "
                            "(MEASURED_PEAKS.json has no FP64 figure)",
             "hbm_gbs": kd["gbs"], "hbm_frac": kd["gbs"] / peak_hbm,
+            "dram_gbs": dram(f"k_{dom}<double>", kd["avg_ms"])[0],
+            "dram_frac": dram(f"k_{dom}<double>", kd["avg_ms"])[1],
             "hbm_peak_source": peak_src}
     f32 = results["fp32"]
     dom32 = max(f32["kernels"], key=lambda k: f32["kernels"][k]["share"])
@@ -358,6 +365,8 @@ def run_native(args):
                          "peak": peak_hbm, "unit": "GB/s", "frac": k32["gbs"] / peak_hbm,
                          "traffic": traffic(f"k_{dom32}<float>"),
                          "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+                         "dram_gbs": dram(f"k_{dom32}<float>", k32["avg_ms"])[0],
+                         "dram_frac": dram(f"k_{dom32}<float>", k32["avg_ms"])[1],
                          "peak_source": peak_src},
             "kernels": f32["kernels"]}},
         "state_finite": r["finite"],
@@ -430,6 +439,23 @@ def run_batched(args):
         value, units, ms = replicas.whole_job_rate(A * 3 * args.steps, e0.elapsed_time(e1), dist,
                                                    device="cuda")
         kms, nl = batch.steps_profiled(U0.clone(), 0.0, args.steps)
+        # roofline of the dominant kernel (per-launch averages of the profiled steps)
+        T = 8 if prec == "fp64" else 4
+        costs = algorithmic_costs(batch.stats_dict(), T)
+        dom = max(("vertex", "edge", "div"), key=lambda k: kms[k])
+        avg_s = kms[dom] / 1000.0 / (3 * args.steps)
+        peak_hbm, peak_src = load_peaks()
+        if prec == "fp64":
+            roof = {"kernel": f"k_{dom}<double>", "bound": "alu",
+                    "achieved": costs[dom]["flops"] / avg_s / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+                    "unit": "TFLOP/s", "traffic": None,
+                    "hbm_gbs": costs[dom]["bytes"] / avg_s / 1e9}
+            roof["frac"] = roof["achieved"] / roof["peak"]
+        else:
+            roof = {"kernel": f"k_{dom}<float>", "bound": "hbm",
+                    "achieved": costs[dom]["bytes"] / avg_s / 1e9, "peak": peak_hbm,
+                    "unit": "GB/s", "traffic": None, "peak_source": peak_src}
+            roof["frac"] = roof["achieved"] / peak_hbm
         del batch, W, X
         torch.cuda.empty_cache()
         # the same meshes one at a time
@@ -452,7 +478,7 @@ def run_batched(args):
                      "looped_singles_ms_per_step": ms_loop / args.steps,
                      "speedup_vs_looped": ms_loop / ms,
                      "launch": {"persistent": choice[0], "grid": choice[1]},
-                     "kernels_ms": kms, "launches": nl}
+                     "kernels_ms": kms, "launches": nl, "roofline": roof}
     if dist is not None:
         dist.destroy_process_group()
     if rank != 0:
