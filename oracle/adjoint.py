@@ -19,12 +19,13 @@ _H = 1e-30
 
 
 def _ghost_transpose(mesh, g):
-    """Adjoint of the ghost refresh: ghost columns pass their (masked) sensitivities to their
-    donors and become zero."""
+    """Adjoint of the ghost refresh: transmissive ghost columns pass their (masked) sensitivities
+    to their donors and become zero; fixed ghosts (donor -1) keep theirs."""
     gid = np.asarray(mesh["ghost_ids"], dtype=np.int64)
     dn = np.asarray(mesh["ghost_donor"], dtype=np.int64)
     fl = np.asarray(mesh["ghost_flags"])
-    g[:, gid[dn < 0]] = 0.0                    # fixed ghosts: given values, no dependence
+    # fixed ghosts (R22) are not overwritten by the refresh: their values are inputs of the
+    # residual like any other column and keep their sensitivities
     gid, dn, fl = gid[dn >= 0], dn[dn >= 0], fl[dn >= 0]
     if len(gid) == 0:
         return g
@@ -86,12 +87,16 @@ def step_vjp(mesh, P, U, dt, lam, opts=None):
     mu3[:, act] = lr[:, act]
     lu = lr - mu3                                  # ghost columns of the result come from u
     lu += mu3 / 3.0
+    # fixed ghost columns (R22) of the stage states are those of u (the residual is zero there)
+    fx = np.asarray(mesh["ghost_ids"], dtype=np.int64)[np.asarray(mesh["ghost_donor"]) < 0]
     lu2 = 2.0 / 3.0 * (mu3 + dt * residual_vjp(mesh, P, u2, mu3, opts))
     m2 = np.zeros_like(lu2)
     m2[:, act] = lu2[:, act]
     lu += 0.75 * m2
+    lu[:, fx] += lu2[:, fx]
     lu1 = 0.25 * (m2 + dt * residual_vjp(mesh, P, u1, m2, opts))
     m1 = np.zeros_like(lu1)
     m1[:, act] = lu1[:, act]
     lu += m1 + dt * residual_vjp(mesh, P, u, m1, opts)
+    lu[:, fx] += lu1[:, fx]
     return _ghost_transpose(mesh, lu)

@@ -686,7 +686,7 @@ def test_linearised_residual_has_growing_modes():
     assert growth > 0.05
 
 
-@pytest.mark.parametrize("kind", ["periodic", "ghosts", "viscous"])
+@pytest.mark.parametrize("kind", ["periodic", "ghosts", "viscous", "conservative", "walls"])
 def test_oracle_adjoint_dot_product_against_complex_step(kind):
     """<lam, J delta> with J delta by the complex-step method through the whole oracle (exact to
     rounding) must equal <J^T lam, delta> from the hand-assembled adjoint, for the residual and
@@ -703,10 +703,19 @@ def test_oracle_adjoint_dot_product_against_complex_step(kind):
         U = synth.uniform_state(m)
         U[:4] *= 1.0 + 0.05 * np.sin(3.0 * m["x"])[None]
         U[4:] = 0.01 * rng.standard_normal((8, U.shape[1]))
-    else:
+    elif kind == "viscous":
         m = synth.jittered_grid(10, 10, 2 * np.pi, 2 * np.pi, seed=3)
         opts = oracle.Options(viscous=True, mu=0.05, R_gas=1.0 / (1.4 * 0.01))
         U = synth.taylor_green(m)
+    elif kind == "conservative":
+        m = synth.jittered_grid(10, 10, 4.0, 4.0, seed=3)
+        opts = oracle.Options(conservative=True)
+        U = synth.isentropic_vortex(m, center=(2.0, 2.0), beta=3.0)
+    else:                                      # fixed wall bands (donor -1), viscous Couette
+        m = synth.couette_channel(8, 9, 6, seed=7)
+        opts = oracle.Options(viscous=True, mu=0.1, prandtl=100.0, R_gas=0.4 * 10.0 / 1.4)
+        U = synth.couette(m)
+        U[:, np.abs(m["y"]) < 5] += 1e-3 * rng.standard_normal((12, int(np.sum(np.abs(m["y"]) < 5))))
     P = oracle.prepare(m, opts)
     V = U.shape[1]
     mu, delta = rng.standard_normal((12, V)), rng.standard_normal((12, V))
