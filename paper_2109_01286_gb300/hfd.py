@@ -369,6 +369,23 @@ class Mesh:
     def check(self, stream=None):
         _ok(_lib.hfd_check(self._h, _stream(stream)), "hfd_check")
 
+    def save_state(self, path, U_internal, **extra):
+        """Checkpoint: writes the state (exported to input vertex order) and the mesh's vertex
+        count to an .npz file, with any extra arrays given by keyword (time, step count, ...)."""
+        U = self.export_state(U_internal).cpu().numpy()
+        np.savez(path, U=U, nv=np.int64(self.nv), **extra)
+
+    def load_state(self, path):
+        """Reads a checkpoint written by save_state; returns (state in internal order on the
+        current CUDA device, dict of the extra arrays)."""
+        import torch
+        with np.load(path) as z:
+            if int(z["nv"]) != self.nv or z["U"].shape != (12, self.nv):
+                raise ValueError(f"checkpoint of {int(z['nv'])} vertices for a mesh of {self.nv}")
+            U = torch.from_numpy(np.ascontiguousarray(z["U"])).cuda()
+            extra = {k: z[k] for k in z.files if k not in ("U", "nv")}
+        return self.import_state(U), extra
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.hfd_mesh_destroy(self._h)

@@ -477,3 +477,23 @@ def test_couette_channel_with_wall_bands_kernel_parity():
         assert np.abs(out[rows] - ref[rows]).max() <= 1e-13 * np.abs(U[rows]).max()
     g = m["ghost_ids"]
     np.testing.assert_array_equal(out[:, g], U[:, g])
+
+
+def test_checkpoint_resume_continues_bit_identically(c1, tmp_path):
+    """save_state / load_state: 4 steps straight equal 2 steps, a checkpoint to .npz, a reload
+    into a new mesh and 2 more steps, bit for bit (CFL step each time)."""
+    pkg = _hfd()
+    m, _, U = c1
+    a = pkg.Mesh(m)
+    X = a.import_state(torch.from_numpy(U).cuda())
+    a.steps(X, 0.0, 4)
+    Y = a.import_state(torch.from_numpy(U).cuda())
+    a.steps(Y, 0.0, 2)
+    a.save_state(tmp_path / "ck.npz", Y, steps=np.int64(2))
+    b = pkg.Mesh(m)
+    Z, extra = b.load_state(tmp_path / "ck.npz")
+    assert int(extra["steps"]) == 2
+    b.steps(Z, 0.0, 2)
+    np.testing.assert_array_equal(a.export_state(X).cpu().numpy(), b.export_state(Z).cpu().numpy())
+    with pytest.raises(ValueError):
+        pkg.Mesh(synth.jittered_grid(8, 8, 1.0, 1.0, seed=0)).load_state(tmp_path / "ck.npz")
