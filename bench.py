@@ -52,10 +52,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="four-quadrant",
-                    choices=["four-quadrant", "batched", "adjoint", "tgv", "conservative"],
+                    choices=["four-quadrant", "batched", "adjoint", "tgv", "conservative",
+                             "circular-sod"],
                     help="batched: 256 uneven isentropic-vortex meshes advanced together; "
                          "adjoint: gradient of a 200-step vortex run, checked by differences; "
-                         "conservative: the four-quadrant line with median-dual value rows")
+                         "conservative: the four-quadrant line with median-dual value rows; "
+                         "circular-sod: Sec. 3.3 on embedded-circle Delaunay meshes")
     ap.add_argument("--directions", type=int, default=64)
     ap.add_argument("--batch", type=int, default=256)
     return ap.parse_args()
@@ -715,6 +717,70 @@ def run_tgv(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ circular Sod workload
+def run_circular_sod(args):
+    """Circular Sod problem (Sec. 3.3) on embedded-circle Delaunay meshes of [-1, 1]^2 whose
+    sides are split into 50, 100 and 150 segments: FP64 SSP-RK3 steps at CFL 0.3 (device time
+    step) toward t = 0.2, stopping at the first step whose state is not finite or has a
+    non-positive density or pressure; then the step rate on the largest mesh, timed over the
+    steps that stay admissible, each timed pass restarting from the initial state (the device
+    copy is inside the timed region)."""
+    import torch
+    from paper_2109_01286_gb300 import Mesh
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    g1 = synth.GAMMA - 1.0
+    runs, last = [], None
+    for n in (50, 100, 150):
+        m = synth.embedded_circle_box(n, seed=8)
+        U0 = torch.from_numpy(synth.circular_sod(m)).cuda()
+        mesh = Mesh(m)
+        A = mesh.stats_dict()["nactive"]
+        X = mesh.import_state(U0)
+        t, steps, first_bad = 0.0, 0, None
+        while t < 0.2 and steps < 5000:
+            mesh.step(X, 0.0)
+            t += mesh.last_dt()
+            steps += 1
+            w = X[:4]
+            p = g1 * (w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0])
+            if not (bool(torch.isfinite(w).all()) and bool((w[0] > 0).all()) and bool((p > 0).all())):
+                first_bad = steps
+                break
+        runs.append({"segments": n, "vertices": len(m["x"]), "active": A,
+                     "triangles": len(m["tri"]), "steps_admissible": steps - (first_bad is not None),
+                     "t_admissible": t if first_bad is None else t - mesh.last_dt(),
+                     "first_inadmissible_step": first_bad, "t_target": 0.2})
+        last = (mesh, A, U0, steps - (first_bad is not None))
+    mesh, A, U0, K = last
+    K = max(1, min(K, 5))
+    Ui = mesh.import_state(U0)
+    X = torch.empty_like(Ui)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        X.copy_(Ui)
+        mesh.steps(X, 0.0, K)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        X.copy_(Ui)
+        mesh.steps(X, 0.0, K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    line = {
+        "metric": "vertex-stage updates/s", "workload": "circular-sod",
+        "value": A * 3 * K * args.steps / (ms / 1000.0), "unit": "vertex-stage/s",
+        "ms_per_step": ms / (K * args.steps), "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "circular Sod (Sec. 3.3), embedded-circle Delaunay meshes of "
+                               "[-1,1]^2 with 50/100/150 segments per side, 5 ghost layers, "
+                               "CFL 0.3; rate on the 150-segment mesh over "
+                               f"{K} steps per pass from the initial state"},
+        "runs": runs,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -725,6 +791,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "tgv":
         run_tgv(args)
+    elif args.workload == "circular-sod":
+        run_circular_sod(args)
     else:
         run_native(args)
 

@@ -106,3 +106,72 @@ def mesh_summary(mesh):
     V = len(mesh["x"])
     return {"vertices": V, "triangles": len(mesh["tri"]), "ghosts": len(mesh["ghost_ids"]),
             "active": V - len(mesh["ghost_ids"])}
+
+
+def embedded_circle_box(n, seed, radius=0.5, half=1.0, ghost=5, jitter=0.15, band=0.5):
+    """Square [-half, half]^2 split into n segments per side with a circle of `radius` embedded
+    at the centre (Sec. 3.3: the circle carries the initial discontinuity, so it is a line of
+    mesh vertices).  Construction:
+      * the (n+1)^2 physical grid vertices, interior ones jittered as in `jittered_box_with_ghosts`,
+        plus `ghost` unjittered ghost layers outside each side (donors as there);
+      * every jittered vertex within band*h of the circle is removed, and round(2 pi radius / h)
+        vertices are placed on the circle at equal angles (the first at angle 0);
+      * the vertices are triangulated by Delaunay (scipy's Qhull).  Exactly cocircular sets
+        (unjittered grid cells) are broken by triangulating on coordinates moved by at most
+        1e-6 h for every unjittered vertex off the outermost ring; the stored coordinates are
+        the exact ones.
+    Returns a mesh dict like the other generators plus "on_circle" (bool per vertex).  Random
+    draws, in order from PCG64(seed): the grid's x and y jitter and diagonal bits (diagonals
+    unused), then the tie-breaking moves (x then y)."""
+    from scipy.spatial import Delaunay
+
+    g = _grid(n + 1, n + 1, (-half, half), (-half, half), False, False, ghost, jitter, seed)
+    h = g["h"][0]
+    NX, NY = g["grid"]
+    x, y = g["x"], g["y"]
+    V = len(x)
+    I = np.arange(V) % NX
+    J = np.arange(V) // NX
+    phys = np.ones(V, bool)
+    phys[g["ghost_ids"]] = False
+    on_bnd = phys & ((I == ghost) | (I == NX - 1 - ghost) | (J == ghost) | (J == NY - 1 - ghost))
+    jittered = phys & ~on_bnd
+    r = np.hypot(x, y)
+    keep = ~(jittered & (np.abs(r - radius) < band * h))
+    if not np.all(keep[~jittered]):
+        raise ValueError("the circle must lie inside the jittered interior")
+    nc = int(round(2.0 * np.pi * radius / h))
+    th = 2.0 * np.pi * np.arange(nc) / nc
+    old = np.nonzero(keep)[0]
+    new_id = np.full(V, -1, np.int64)
+    new_id[old] = np.arange(len(old))
+    xs = np.concatenate([x[old], radius * np.cos(th)])
+    ys = np.concatenate([y[old], radius * np.sin(th)])
+    on_circle = np.concatenate([np.zeros(len(old), bool), np.ones(nc, bool)])
+    fixed = np.concatenate([~jittered[old], np.zeros(nc, bool)])
+    outer = np.concatenate([(I[old] == 0) | (I[old] == NX - 1) | (J[old] == 0) | (J[old] == NY - 1),
+                            np.zeros(nc, bool)])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rng.uniform(size=2 * V)                      # the grid's jitter draws
+    rng.integers(0, 2, (NX - 1) * (NY - 1))      # the grid's diagonal bits
+    move = fixed & ~outer
+    tx = xs + np.where(move, rng.uniform(-1.0, 1.0, len(xs)), 0.0) * 1e-6 * h
+    ty = ys + np.where(move, rng.uniform(-1.0, 1.0, len(xs)), 0.0) * 1e-6 * h
+    dl = Delaunay(np.stack([tx, ty], 1))
+    if len(dl.coplanar):
+        raise RuntimeError("Delaunay left vertices out of the triangulation")
+    tri = dl.simplices.astype(np.int64)
+    a = ((xs[tri[:, 1]] - xs[tri[:, 0]]) * (ys[tri[:, 2]] - ys[tri[:, 0]])
+         - (xs[tri[:, 2]] - xs[tri[:, 0]]) * (ys[tri[:, 1]] - ys[tri[:, 0]]))
+    tri[a < 0] = tri[a < 0][:, [0, 2, 1]]
+    gid = new_id[g["ghost_ids"]]
+    donor = new_id[g["ghost_donor"]]
+    if np.any(gid < 0) or np.any(donor < 0):
+        raise RuntimeError("a ghost or donor vertex was removed")
+    return {
+        "x": xs, "y": ys, "tri": tri.astype(np.int32),
+        "Lx": 2.0 * half, "Ly": 2.0 * half, "periodic_x": False, "periodic_y": False,
+        "ghost_ids": gid.astype(np.int32), "ghost_donor": donor.astype(np.int32),
+        "ghost_flags": g["ghost_flags"], "grid": (NX, NY), "h": (h, h), "seed": seed,
+        "on_circle": on_circle, "radius": radius,
+    }

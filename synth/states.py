@@ -79,6 +79,19 @@ def planar_sod(mesh, gamma=GAMMA, x0=0.5, left=(1.0, 0.0, 0.0, 1.0), right=(0.12
     return _piecewise(mesh, [left, right], region, gamma)
 
 
+def circular_sod(mesh, gamma=GAMMA, radius=0.5, inside=(1.0, 0.0, 0.0, 1.0),
+                 outside=(0.125, 0.0, 0.0, 0.1)):
+    """Circular Sod problem of Sec. 3.3: the inside state where |r| < radius, the outside state
+    elsewhere; zero derivatives.  The circle's own vertices (mesh["on_circle"], placed exactly
+    on it by `embedded_circle_box`) take the outside state, as the strict inequality says.  The
+    outside velocity printed in the paper is garbled; it is read as 0 (at rest)."""
+    r = np.hypot(mesh["x"], mesh["y"])
+    region = (r >= radius).astype(int)
+    if "on_circle" in mesh:
+        region[mesh["on_circle"]] = 1
+    return _piecewise(mesh, [inside, outside], region, gamma)
+
+
 def taylor_green(mesh, mach=0.1, gamma=GAMMA):
     """Decaying Taylor-Green vortex initial state on [0, 2pi]^2: u = sin x cos y,
     v = -cos x sin y, rho = 1, p = p0 + (cos 2x + cos 2y)/4 with p0 = 1/(gamma M^2)."""

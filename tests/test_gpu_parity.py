@@ -497,3 +497,58 @@ def test_checkpoint_resume_continues_bit_identically(c1, tmp_path):
     np.testing.assert_array_equal(a.export_state(X).cpu().numpy(), b.export_state(Z).cpu().numpy())
     with pytest.raises(ValueError):
         pkg.Mesh(synth.jittered_grid(8, 8, 1.0, 1.0, seed=0)).load_state(tmp_path / "ck.npz")
+
+
+@pytest.fixture(scope="module")
+def csod():
+    m = synth.embedded_circle_box(24, seed=8)
+    P = oracle.prepare(m)
+    U = synth.circular_sod(m)
+    return m, P, U
+
+
+def test_circular_sod_delaunay_mesh_kernel_parity(csod):
+    """Sec. 3.3 circular Sod on the embedded-circle Delaunay mesh: residual and five SSP-RK3
+    steps with the device CFL step against the oracle (kernel parity).  The discontinuity lies
+    on a mesh line, so the WENO branch is taken all around the circle."""
+    pkg = _hfd()
+    m, P, U = csod
+    mesh = _kernel_mesh(pkg, m, P)
+    R = _residual(mesh, U)
+    R_ref = oracle.residual(m, P, U.copy())
+    d = {}
+    oracle.hfd_oracle.edge_values(P, U.copy(), P.opts, d)
+    assert sum(int((~s).sum()) for s in d["smooth"]) > 50
+    bad = near_threshold_vertices(m, P, U, P.opts)
+    keep = np.setdiff1d(P.active, bad)
+    assert len(keep) > 0.95 * len(P.active)
+    assert max(rel_l2_groups(R, R_ref, keep)) < TOL_FP64
+    X = mesh.import_state(torch.from_numpy(U).cuda())
+    ref = U.copy()
+    for _ in range(5):
+        dt = oracle.cfl_dt(m, P, ref)
+        ref = oracle.step(m, P, ref, dt)
+        mesh.step(X, 0.0)
+        assert abs(mesh.last_dt() - dt) <= 1e-12 * dt
+    out = mesh.export_state(X).cpu().numpy()
+    err = rel_l2_groups(out - U, ref - U)
+    assert max(err) < 1e-10, err
+    mesh.check()
+
+
+@pytest.mark.parametrize("precision,margin,tol", [("fp64", 1e-5, 1e-6), ("fp32", 1e-3, 1e-4)])
+def test_circular_sod_delaunay_mesh_full_path(csod, precision, margin, tol):
+    """The library's own coefficients (and the FP32-bulk path) on the Delaunay mesh: residual
+    against the oracle's.  Vertices reading an edge whose sensor lies within `margin` of a
+    threshold are left out: the coefficient differences (FP64, up to ~1e-7 on a few truncated
+    pseudo-inverses) or FP32 data may decide those branches either way."""
+    pkg = _hfd()
+    m, P, U = csod
+    mesh = pkg.Mesh(m, precision=precision)
+    R = _residual(mesh, U)
+    R_ref = oracle.residual(m, P, U.copy())
+    bad = near_threshold_vertices(m, P, U, P.opts, margin=margin)
+    keep = np.setdiff1d(P.active, bad)
+    assert len(keep) > 0.8 * len(P.active)
+    err = rel_l2_groups(R, R_ref, keep)
+    assert max(err) < tol, err

@@ -132,6 +132,27 @@ def test_host_prep_with_ghosts_matches_oracle(pkg):
     np.testing.assert_array_equal(prep.get("active"), P.active)
 
 
+def test_host_prep_on_embedded_circle_delaunay_mesh_matches_oracle(pkg):
+    """A Delaunay mesh (Sec. 3.3 circular Sod, vertex valences 4-9, a ring of vertices on the
+    circle) instead of a split grid: same discrete choices and coefficients."""
+    m = synth.embedded_circle_box(16, seed=8)
+    P = oracle.prepare(m)
+    prep = pkg.Prep(m)
+    from gpu_helpers import oracle_blocks
+    np.testing.assert_array_equal(prep.get("edges").reshape(-1, 2), P.topo["edges"])
+    np.testing.assert_array_equal(prep.get("flux_edges"), P.edges)
+    np.testing.assert_array_equal(prep.get("stencil").reshape(-1, 6), P.stencil)
+    np.testing.assert_array_equal(prep.get("rank").reshape(-1, 2), P.rank)
+    np.testing.assert_array_equal(prep.get("active"), P.active)
+    np.testing.assert_array_equal(prep.get("div_degree"), P.div_degree)
+    deg = np.bincount(np.asarray(P.topo["edges"]).ravel(), minlength=len(m["x"]))
+    assert deg[P.active].min() <= 4 and deg[P.active].max() >= 8
+    ref = oracle_blocks(P, len(m["x"]))["div_coef"]
+    assert np.abs(prep.get("div_coef") - ref).max() < 1e-11 * np.abs(ref).max()
+    d = np.abs(prep.get("w5").reshape(-1, 2, 15) - P.w5).max(axis=(1, 2))
+    assert np.median(d) < 1e-12 and d.max() < 1e-6
+
+
 def test_allocator_and_flux_options_are_checked(pkg):
     with pytest.raises(ValueError):
         pkg.options(allocator="malloc")
