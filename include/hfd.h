@@ -275,11 +275,23 @@ hfd_status hfd_mesh_set_launch(hfd_mesh* mesh, int32_t persistent, int32_t grid)
  * HFD_ERR_TIMEOUT in the error word and returns instead of waiting.  Drops captured graphs. */
 hfd_status hfd_mesh_set_barrier_limit(hfd_mesh* mesh, uint32_t polls);
 
+/* Lanes (threads) per vertex in the divergence gather: 1, 2, 4 or 8.  The defaults are 1 for
+ * FP64 meshes (FP64-pipe bound: no cross-lane reduction) and 4 for FP32 meshes (memory bound:
+ * coalesced groups); small meshes fill the GPU better with more lanes.  Each lane sums a
+ * strided share of the entries and the shares are combined by a fixed reduce-scatter, so a lane
+ * count gives deterministic results that agree with the other counts to rounding.  The
+ * persistent form (hfd_mesh_set_launch) has kernels for 1, 2 and 4 lanes and runs 8 as 4.  Drops
+ * captured graphs.  Errors: HFD_ERR_ARG (another count, or a persistent grid set by
+ * hfd_mesh_set_launch that the new count's kernel cannot hold co-resident). */
+hfd_status hfd_mesh_set_lanes(hfd_mesh* mesh, int32_t lanes);
+
 /* Autotuner: times one Runge-Kutta stage on (a copy of) the device state U, internal order,
- * for the four-launch form and for the persistent form at every co-resident block count, keeps
- * the fastest, and writes it to choice[0] (persistent) and choice[1] (grid) if choice is not
- * NULL.  The choice changes the launch shape, not the method's arithmetic (results agree to
- * rounding, see hfd_mesh_set_launch).  Synchronises. */
+ * for every lane count of hfd_mesh_set_lanes in the four-launch form and for 1, 2 and 4 lanes
+ * in the persistent form at every co-resident block count; keeps the fastest, and writes it to
+ * choice[0] (persistent), choice[1] (grid) and choice[2] (lanes) if choice (3 int32, caller
+ * owned) is not NULL.  The choice changes the launch shape and the divergence's summation
+ * order, not the method's arithmetic (results agree to rounding, see hfd_mesh_set_launch and
+ * hfd_mesh_set_lanes).  Synchronises. */
 hfd_status hfd_mesh_autotune(hfd_mesh* mesh, const double* U, void* stream, int32_t* choice);
 
 /* dt used by the most recent step, one value per member mesh (synchronises the stream). */

@@ -582,6 +582,25 @@ hfd_status hfd_mesh_set_launch(hfd_mesh* m, int32_t persistent, int32_t grid) {
   return HFD_OK;
 }
 
+hfd_status hfd_mesh_set_lanes(hfd_mesh* m, int32_t lanes) {
+  if (!m || !(lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8)) {
+    set_error("hfd_mesh_set_lanes: lanes must be 1, 2, 4 or 8");
+    return HFD_ERR_ARG;
+  }
+  if (m->persistent && m->grid > 0) {
+    int per_sm = 0, nsm = 0;
+    CK(hfd::persistent_max_blocks(m->dm, lanes, &per_sm, &nsm));
+    if (m->grid > per_sm * nsm) {
+      set_error("hfd_mesh_set_lanes: the persistent grid of %d blocks exceeds the %d co-resident "
+                "blocks at %d lanes", m->grid, per_sm * nsm, lanes);
+      return HFD_ERR_ARG;
+    }
+  }
+  m->lanes = lanes;
+  drop_graphs(m);
+  return HFD_OK;
+}
+
 hfd_status hfd_mesh_set_barrier_limit(hfd_mesh* m, uint32_t polls) {
   if (!m) { set_error("hfd_mesh_set_barrier_limit: null mesh"); return HFD_ERR_ARG; }
   m->dm.barrier_spins = polls;
@@ -595,11 +614,17 @@ hfd_status hfd_mesh_autotune(hfd_mesh* m, const double* U, void* stream, int32_t
   const DevMesh& d = m->dm;
   size_t bytes = (size_t)12 * d.V * sizeof(double);
   CK(cudaMemcpyAsync(m->U1, U, bytes, cudaMemcpyDeviceToDevice, s));
-  int per_sm = 0, nsm = 0;
-  CK(hfd::persistent_max_blocks(d, m->lanes, &per_sm, &nsm));
-  struct Cand { int persistent, grid; };
-  std::vector<Cand> cands = {{0, 0}};
-  for (int b = 1; b <= per_sm; ++b) cands.push_back({1, b * nsm});
+  // candidates: lanes per vertex in the divergence x (four-launch form, persistent form at
+  // every co-resident block count for those lanes)
+  struct Cand { int persistent, grid, lanes; };
+  std::vector<Cand> cands;
+  for (int lanes : {1, 2, 4, 8}) {
+    int per_sm = 0, nsm = 0;
+    CK(hfd::persistent_max_blocks(d, lanes, &per_sm, &nsm));
+    cands.push_back({0, 0, lanes});
+    if (lanes == 8) continue;                  // the persistent kernel runs 8 lanes as 4
+    for (int b = 1; b <= per_sm; ++b) cands.push_back({1, b * nsm, lanes});
+  }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -613,12 +638,12 @@ hfd_status hfd_mesh_autotune(hfd_mesh* m, const double* U, void* stream, int32_t
       if (c.persistent) {
         CK(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
         CK(hfd::launch_stage_persistent(d, m->U1, m->U1, m->U2, hfd::DIV_STAGE, 0.0, 1.0, dt,
-                                        m->ph, m->lanes, c.grid, true, s));
+                                        m->ph, c.lanes, c.grid, true, s));
       } else {
         if (d.G) CK(hfd::launch_ghost(d, m->U1, m->U1, s));
         CK(hfd::launch_vertex(d, m->U1, m->ph, s));
         CK(hfd::launch_edge(d, m->ph, s));
-        CK(hfd::launch_div(d, m->U1, m->U1, m->U2, hfd::DIV_STAGE, 0.0, 1.0, dt, m->ph, m->lanes, s));
+        CK(hfd::launch_div(d, m->U1, m->U1, m->U2, hfd::DIV_STAGE, 0.0, 1.0, dt, m->ph, c.lanes, s));
       }
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
@@ -636,8 +661,9 @@ hfd_status hfd_mesh_autotune(hfd_mesh* m, const double* U, void* stream, int32_t
   CK(cudaMemsetAsync(d.err, 0, sizeof(unsigned), s));
   m->persistent = pick.persistent;
   m->grid = pick.grid;
+  m->lanes = pick.lanes;
   drop_graphs(m);
-  if (choice) { choice[0] = pick.persistent; choice[1] = pick.grid; }
+  if (choice) { choice[0] = pick.persistent; choice[1] = pick.grid; choice[2] = pick.lanes; }
   return HFD_OK;
 }
 

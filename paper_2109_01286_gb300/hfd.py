@@ -27,7 +27,7 @@ EXPORTED = ["hfd_default_options", "hfd_last_error", "hfd_prep_create", "hfd_pre
             "hfd_mesh_destroy", "hfd_mesh_info", "hfd_mesh_perm", "hfd_state_import",
             "hfd_state_export", "hfd_residual", "hfd_step", "hfd_steps", "hfd_steps_host",
             "hfd_last_dt", "hfd_check", "hfd_steps_profiled", "hfd_residual_static",
-            "hfd_prep_concat", "hfd_mesh_set_launch", "hfd_mesh_autotune",
+            "hfd_prep_concat", "hfd_mesh_set_launch", "hfd_mesh_set_lanes", "hfd_mesh_autotune",
             "hfd_mesh_set_barrier_limit", "hfd_adjoint", "hfd_batch_create", "hfd_batch_destroy",
             "hfd_batch_mesh", "hfd_batch_step"]
 
@@ -120,6 +120,7 @@ _lib.hfd_prep_concat.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POIN
 _lib.hfd_mesh_set_launch.argtypes = [_P, ctypes.c_int32, ctypes.c_int32]
 _lib.hfd_mesh_autotune.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int32)]
 _lib.hfd_mesh_set_barrier_limit.argtypes = [_P, ctypes.c_uint32]
+_lib.hfd_mesh_set_lanes.argtypes = [_P, ctypes.c_int32]
 _lib.hfd_adjoint.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
 _lib.hfd_step.argtypes = [_P, _P, ctypes.c_double, _P]
 _lib.hfd_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32,
@@ -353,11 +354,16 @@ class Mesh:
     def set_barrier_limit(self, polls):
         _ok(_lib.hfd_mesh_set_barrier_limit(self._h, int(polls)), "hfd_mesh_set_barrier_limit")
 
+    def set_lanes(self, lanes):
+        """Lanes per vertex in the divergence gather (1, 2, 4 or 8)."""
+        _ok(_lib.hfd_mesh_set_lanes(self._h, int(lanes)), "hfd_mesh_set_lanes")
+
     def autotune(self, U, stream=None):
-        """Pick the fastest launch shape for one RK stage on state U; returns (persistent, grid)."""
-        c = (ctypes.c_int32 * 2)()
+        """Pick the fastest launch shape for one RK stage on state U; returns
+        (persistent, grid, lanes)."""
+        c = (ctypes.c_int32 * 3)()
         _ok(_lib.hfd_mesh_autotune(self._h, _dptr(U), _stream(stream), c), "hfd_mesh_autotune")
-        return int(c[0]), int(c[1])
+        return int(c[0]), int(c[1]), int(c[2])
 
     def last_dt(self, stream=None):
         """dt of the last step: a float, or one value per member for a batch."""

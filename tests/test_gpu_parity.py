@@ -552,3 +552,29 @@ def test_circular_sod_delaunay_mesh_full_path(csod, precision, margin, tol):
     assert len(keep) > 0.8 * len(P.active)
     err = rel_l2_groups(R, R_ref, keep)
     assert max(err) < tol, err
+
+
+def test_lane_setter_and_autotuner_keep_results_to_rounding(c1):
+    """hfd_mesh_set_lanes changes only the divergence's summation order; an invalid count is
+    refused; the autotuner's pick (launch form, grid, lanes) steps to the default's rounding."""
+    pkg = _hfd()
+    m, P, U = c1
+    mesh = pkg.Mesh(m)
+    R1 = _residual(mesh, U)
+    for lanes in (8, 2, 1):
+        mesh.set_lanes(lanes)
+        R = _residual(mesh, U)
+        assert max(rel_l2_groups(R, R1)) < 1e-13, lanes
+    with pytest.raises(pkg.HfdError) as e:
+        mesh.set_lanes(3)
+    assert e.value.status == 1
+    Ui = mesh.import_state(torch.from_numpy(U).cuda())
+    a = Ui.clone()
+    mesh.steps(a, 0.0, 3)
+    persistent, grid, lanes = mesh.autotune(Ui)
+    assert persistent in (0, 1) and lanes in (1, 2, 4, 8) and grid >= 0
+    b = Ui.clone()
+    mesh.steps(b, 0.0, 3)
+    torch.cuda.synchronize()
+    mesh.check()
+    assert (torch.linalg.norm(a - b) / torch.linalg.norm(a)).item() < 1e-12
