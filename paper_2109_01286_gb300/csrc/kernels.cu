@@ -169,9 +169,10 @@ __device__ __forceinline__ void roe_flux(const T* wl, const T* wr, T nx, T ny, T
   // they equal the left-eigenvector products (Roe's own form of the solver)
   T rho = rl * rr, dp = pr - pl, drho = wr[0] - wl[0];
   T dun = (ur - ul) * nx + (vr - vl) * ny, dut = (vr - vl) * nx - (ur - ul) * ny;
-  T ic2 = ic * ic, hc2 = T(0.5) * ic2;
+  // the strengths carry the factor 1/2 of the flux formula h = (f_l + f_r)/2 - R |Lambda| a / 2
+  T ic2 = ic * ic, hc2 = T(0.5) * ic2, qc2 = T(0.25) * ic2;
   T rcd = rho * c * dun;
-  T a[4] = {(dp - rcd) * hc2, drho - dp * ic2, rho * dut, (dp + rcd) * hc2};
+  T a[4] = {(dp - rcd) * qc2, T(0.5) * drho - dp * hc2, (T(0.5) * rho) * dut, (dp + rcd) * qc2};
   T lam[4] = {qn - c, qn, qn, qn + c};
   T del = harten * c, i2del = half_inv_harten * ic;
   T k[4];
@@ -187,7 +188,7 @@ __device__ __forceinline__ void roe_flux(const T* wl, const T* wr, T nx, T ny, T
   T fl[4] = {wl[0] * unl, wl[1] * unl + pl * nx, wl[2] * unl + pl * ny, (wl[3] + pl) * unl};
   T fr[4] = {wr[0] * unr, wr[1] * unr + pr * nx, wr[2] * unr + pr * ny, (wr[3] + pr) * unr};
 #pragma unroll
-  for (int i = 0; i < 4; ++i) hq[i] = T(0.5) * (fl[i] + fr[i]) - T(0.5) * diss[i];
+  for (int i = 0; i < 4; ++i) hq[i] = T(0.5) * (fl[i] + fr[i]) - diss[i];
 }
 
 // Rusanov's (local Lax-Friedrichs) flux along n: the mean of the two normal fluxes minus half
@@ -596,6 +597,12 @@ __device__ __forceinline__ void div_gather_chunked(
   }
 }
 
+// Finite (not inf or NaN) by the exponent field, on the integer pipe (GB300's FP64 pipe is
+// the limit of the FP64 divergence).
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu) != 0x7ffu;
+}
+
 template <typename T, int G, bool VISC>
 __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __restrict__ vptr,
                                          const int32_t* __restrict__ vidx,
@@ -722,7 +729,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
       if (a != 0.0) o += a * Un[idx];   // the first stage does not read the base state
     }
     out[idx] = o;
-    if (!isfinite(o)) bad |= ERRBIT_NONFINITE;
+    if (!finite_bits(o)) bad |= ERRBIT_NONFINITE;
     if (mode == DIV_STAGE && k == 0 && !(o > 0.0)) bad |= ERRBIT_POSITIVITY;
   }
   if (bad) atomicOr(err, bad);
