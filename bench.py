@@ -38,7 +38,7 @@ FP64_PEAK_FLOPS = 1.258e12       # GB300 FP64: 152 SMs x 2 DFMA/clk (ncu peak_su
 CPU_PATCH_N = 32                 # bounded oracle sample: 32 x 32 patch of the same workload
 # DRAM bytes (read + write) per launch on the default 1024 x 1024 workload, from one ncu capture
 # of the current kernels (profiles/traffic_four_quadrant_1024x1024.md); other sizes report null
-DRAM_TRAFFIC_1024 = {"k_div<double>": 3263.9e6, "k_edge<double>": 1090.5e6,
+DRAM_TRAFFIC_1024 = {"k_div<double>": 3264.2e6, "k_edge<double>": 1090.3e6,
                      "k_div<float>": 1755.4e6, "k_edge<float>": 580.6e6}
 
 
