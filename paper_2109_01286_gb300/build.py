@@ -1,8 +1,10 @@
-"""Builds the in-tree shared library `_lib/libhfd.so` (CUDA for sm_103a + host C++).
+"""Builds the in-tree shared libraries `_lib/libhfd.so` (CUDA for sm_103a + host C++) and
+`_lib/libhfd_check.so`, the bounds-checked build of the same library.
 
-Three translation units compile in parallel: csrc/prep.cpp (g++), csrc/kernels.cu and
-csrc/api.cu (nvcc, -gencode arch=compute_103a,code=sm_103a), then nvcc links them with the
-CUDA runtime.  Host code is built with -ffp-contract=off (see csrc/prep.cpp) and without
+The translation units compile in parallel: csrc/prep.cpp (g++), the .cu files (nvcc,
+-gencode arch=compute_103a,code=sm_103a), and csrc/kernels.cu once more with -DHFD_CHECK=1
+(every gathered index tested on the device, see chk_idx in kernels.cu); then nvcc links each
+library with the CUDA runtime.  Host code is built with -ffp-contract=off (see csrc/prep.cpp) and without
 machine-specific flags, so the x86 and Arm builds compute the same host results.
 """
 import os
@@ -16,6 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libhfd.so")
+LIB_CHECK = os.path.join(OUT_DIR, "libhfd_check.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -37,9 +40,9 @@ def _deps():
 
 
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(LIB_CHECK)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_CHECK))
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
@@ -63,6 +66,10 @@ def build(force=False, verbose=False):
         else:
             cmds.append([nvcc, ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off"] +
                         common + ["-c", src, "-o", obj])
+    kcheck = os.path.join(bdir, "kernels_check.cu.o")
+    cmds.append([nvcc, ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-DHFD_CHECK=1"] +
+                common + ["-c", os.path.join(CSRC, "kernels.cu"), "-o", kcheck])
+    objs_check = [kcheck if o.endswith(os.sep + "kernels.cu.o") else o for o in objs]
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
              for c in cmds]
     failed = []
@@ -75,12 +82,13 @@ def build(force=False, verbose=False):
     if failed:
         msg = "\n".join(f"$ {c}\n{o}" for c, o in failed)
         raise RuntimeError(f"libhfd build failed:\n{msg}")
-    tmp = LIB + ".tmp"
-    link = [nvcc, ARCH, "-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
-    p = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
-    if p.returncode != 0:
-        raise RuntimeError(f"libhfd link failed:\n$ {' '.join(link)}\n{p.stdout}")
-    os.replace(tmp, LIB)
+    for out, ob in ((LIB_CHECK, objs_check), (LIB, objs)):
+        tmp = out + ".tmp"
+        link = [nvcc, ARCH, "-shared", "-o", tmp] + ob + ["-lcudart", "-lpthread"]
+        p = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+        if p.returncode != 0:
+            raise RuntimeError(f"{os.path.basename(out)} link failed:\n$ {' '.join(link)}\n{p.stdout}")
+        os.replace(tmp, out)
     return LIB
 
 

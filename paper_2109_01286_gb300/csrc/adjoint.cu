@@ -574,6 +574,7 @@ extern "C" hfd_status hfd_adjoint(hfd_mesh* m, const double* U_n, const double* 
     set_error("hfd_adjoint: invalid argument (dt must be positive, lam_n distinct from lam_np1)");
     return HFD_ERR_ARG;
   }
+  hfd::NvtxRange range("hfd_adjoint");
   const hfd::DevMesh& d = m->dm;
   if (d.precision != 0 || d.viscous || d.G != 0 || d.nmember != 1 || m->ph.flux != 0) {
     set_error("hfd_adjoint: built for FP64 inviscid single meshes without ghosts, Roe flux");

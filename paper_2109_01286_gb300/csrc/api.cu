@@ -373,7 +373,9 @@ hfd_status step_impl(hfd_mesh* m, double* U, double dt, cudaStream_t s, Timer* t
   static const double A_[3] = {0.0, 0.75, 1.0 / 3.0}, B_[3] = {1.0, 0.25, 2.0 / 3.0};
   double* in[3] = {U, m->U1, m->U2};
   double* out[3] = {m->U1, m->U2, U};
+  static const char* const kStage[3] = {"hfd stage 1", "hfd stage 2", "hfd stage 3"};
   for (int k = 0; k < 3; ++k) {
+    hfd::NvtxRange range(kStage[k]);
     if (m->persistent) {
       int grid = m->grid;
       if (grid <= 0) {
@@ -416,6 +418,7 @@ hfd_status hfd_mesh_upload(const hfd_prep* prep, int32_t precision, hfd_mesh** o
     return HFD_ERR_ARG;
   }
   *out = nullptr;
+  hfd::NvtxRange range("hfd_mesh_upload");
   hfd_mesh* m = new (std::nothrow) hfd_mesh();
   if (!m) { set_error("hfd_mesh_upload: out of host memory"); return HFD_ERR_ARG; }
   hfd_status st;
@@ -477,17 +480,20 @@ hfd_status hfd_state_export(hfd_mesh* m, const double* Uint, double* Uin, void* 
 
 hfd_status hfd_residual(hfd_mesh* m, double* U, double* R, void* stream) {
   if (!m || !U || !R || U == R) { set_error("hfd_residual: invalid argument"); return HFD_ERR_ARG; }
+  hfd::NvtxRange range("hfd_residual");
   return residual_impl(m, U, R, (cudaStream_t)stream);
 }
 
 hfd_status hfd_step(hfd_mesh* m, double* U, double dt, void* stream) {
   if (!m || !U) { set_error("hfd_step: invalid argument"); return HFD_ERR_ARG; }
+  hfd::NvtxRange range("hfd_step");
   return step_impl(m, U, dt, (cudaStream_t)stream);
 }
 
 hfd_status hfd_steps(hfd_mesh* m, double* U, double dt, int32_t nsteps, void* stream) {
   if (!m || !U || nsteps < 0) { set_error("hfd_steps: invalid argument"); return HFD_ERR_ARG; }
   if (nsteps == 0) return HFD_OK;
+  hfd::NvtxRange range("hfd_steps");
   auto key = std::make_pair((const double*)U, dt > 0.0 ? dt : 0.0);
   GraphEntry& g = m->graphs[key];
   if (!g.exec) {
@@ -548,6 +554,7 @@ hfd_status hfd_steps_host(hfd_mesh* m, const double* U_in, double* U_out, double
     set_error("hfd_steps_host: invalid argument");
     return HFD_ERR_ARG;
   }
+  hfd::NvtxRange range("hfd_steps_host");
   size_t bytes = (size_t)12 * m->dm.V * sizeof(double);
   if (!m->Uin) {
     TRY(dev_alloc(m, (void**)&m->Uin, bytes));
@@ -610,6 +617,7 @@ hfd_status hfd_mesh_set_barrier_limit(hfd_mesh* m, uint32_t polls) {
 
 hfd_status hfd_mesh_autotune(hfd_mesh* m, const double* U, void* stream, int32_t* choice) {
   if (!m || !U) { set_error("hfd_mesh_autotune: invalid argument"); return HFD_ERR_ARG; }
+  hfd::NvtxRange range("hfd_mesh_autotune");
   cudaStream_t s = (cudaStream_t)stream;
   const DevMesh& d = m->dm;
   size_t bytes = (size_t)12 * d.V * sizeof(double);
@@ -682,6 +690,10 @@ hfd_status hfd_check(hfd_mesh* m, void* stream) {
   CK(cudaMemcpyAsync(&w, m->dm.err, sizeof w, cudaMemcpyDeviceToHost, s));
   CK(cudaMemsetAsync(m->dm.err, 0, sizeof(unsigned), s));
   CK(cudaStreamSynchronize(s));
+  if (w & 8u) {
+    set_error("device error word: a gathered index out of range (bounds-checked build)");
+    return HFD_ERR_MESH;
+  }
   if (w & 1u) { set_error("device error word: non-finite value"); return HFD_ERR_NONFINITE; }
   if (w & 4u) { set_error("device error word: a grid barrier wait timed out"); return HFD_ERR_TIMEOUT; }
   if (w & 2u) { set_error("device error word: rho <= 0 after a stage"); return HFD_ERR_POSITIVITY; }
@@ -751,6 +763,7 @@ extern "C" hfd_status hfd_batch_mesh(hfd_batch* b, hfd_mesh** mesh) {
 extern "C" hfd_status hfd_batch_step(hfd_batch* b, double* const* U, const double* dt,
                                      void* stream) {
   if (!b || !U) { set_error("hfd_batch_step: invalid argument"); return HFD_ERR_ARG; }
+  hfd::NvtxRange range("hfd_batch_step");
   for (int k = 0; k < b->n; ++k) {
     if (!U[k]) { set_error("hfd_batch_step: member %d has no state", k); return HFD_ERR_ARG; }
     if (dt && !(dt[k] > 0.0)) {

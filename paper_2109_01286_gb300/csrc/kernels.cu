@@ -25,7 +25,24 @@
 
 namespace hfd {
 
-enum : unsigned { ERRBIT_NONFINITE = 1u, ERRBIT_POSITIVITY = 2u, ERRBIT_TIMEOUT = 4u };
+enum : unsigned { ERRBIT_NONFINITE = 1u, ERRBIT_POSITIVITY = 2u, ERRBIT_TIMEOUT = 4u, ERRBIT_INDEX = 8u };
+
+// Bounds-checked build (compiled with -DHFD_CHECK=1, the stand-in for a memory checker): every
+// gathered index is tested against its array's extent; one outside [0, n) records ERRBIT_INDEX
+// in the mesh's error word and is replaced by 0, so that the access stays in bounds (the result
+// is then wrong, and hfd_check reports it).  In the normal build this is the identity.
+#ifndef HFD_CHECK
+#define HFD_CHECK 0
+#endif
+__device__ __forceinline__ int chk_idx(int i, int n, unsigned* err) {
+#if HFD_CHECK
+  if ((unsigned)i >= (unsigned)n) {
+    atomicOr(err, ERRBIT_INDEX);
+    return 0;
+  }
+#endif
+  return i;
+}
 
 // ------------------------------------------------------------------ vector loads
 __device__ __forceinline__ void ld12(const double* p, double* o) {
@@ -315,15 +332,15 @@ __device__ __forceinline__ void sensor64(T u0, T u1, T u2, T u3, T u4, const Phy
 }
 
 template <typename T>
-__device__ __forceinline__ void edge_body(int e, int Ef, const int32_t* __restrict__ sten,
+__device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* __restrict__ sten,
                                           const T* __restrict__ nrm, const T* __restrict__ w5,
                                           const T* __restrict__ w3, const T* __restrict__ Ua,
-                                          T* __restrict__ h, const Phys& ph) {
+                                          T* __restrict__ h, const Phys& ph, unsigned* err) {
   if (e >= Ef) return;
   const T g1 = phys_g1<T>(ph);
   int s[6];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) s[k] = ld_stream(sten + (size_t)k * Ef + e);
+  for (int k = 0; k < 6; ++k) s[k] = chk_idx(ld_stream(sten + (size_t)k * Ef + e), V, err);
   T nx = ld_stream(nrm + e), ny = ld_stream(nrm + Ef + e);
   T wi[4], wj[4];
   {
@@ -457,11 +474,11 @@ template <>
 struct EdgeOcc<float> { static constexpr int kMinBlocks = 5; };
 
 template <typename T>
-__global__ void __launch_bounds__(128, EdgeOcc<T>::kMinBlocks) k_edge(int Ef, const int32_t* __restrict__ sten,
+__global__ void __launch_bounds__(128, EdgeOcc<T>::kMinBlocks) k_edge(int Ef, int V, const int32_t* __restrict__ sten,
                                               const T* __restrict__ nrm, const T* __restrict__ w5,
                                               const T* __restrict__ w3, const T* __restrict__ Ua,
-                                              T* __restrict__ h, Phys ph) {
-  edge_body<T>(blockIdx.x * blockDim.x + threadIdx.x, Ef, sten, nrm, w5, w3, Ua, h, ph);
+                                              T* __restrict__ h, Phys ph, unsigned* err) {
+  edge_body<T>(blockIdx.x * blockDim.x + threadIdx.x, Ef, V, sten, nrm, w5, w3, Ua, h, ph, err);
 }
 
 // ------------------------------------------------------------------ k_div
@@ -530,7 +547,8 @@ __device__ __forceinline__ int i4c(const int4& v, int i) {
 
 template <int G, bool VISC>
 __device__ __forceinline__ void div_gather_chunked(
-    int r, int lane, const int32_t* __restrict__ vptr, const int32_t* __restrict__ vidx,
+    int r, int lane, int V, int Ef, unsigned* err, const int32_t* __restrict__ vptr,
+    const int32_t* __restrict__ vidx,
     const int32_t* __restrict__ eptr, const int32_t* __restrict__ eidx,
     const float* __restrict__ cv, const float* __restrict__ ce, const float* __restrict__ cvis,
     const float* __restrict__ FG, const float* __restrict__ FGv, const float* __restrict__ h,
@@ -548,7 +566,7 @@ __device__ __forceinline__ void div_gather_chunked(
 #pragma unroll
     for (int q4 = 0; q4 < 4; ++q4) {
       float f[8];
-      ld8(FG + (size_t)i4c(u, q4) * 8, f);
+      ld8(FG + (size_t)chk_idx(i4c(u, q4), V, err) * 8, f);
       const float c0f = f4c(k[0], q4), c0g = f4c(k[1], q4), cxf = f4c(k[2], q4);
       const float cxg = f4c(k[3], q4), cyf = f4c(k[4], q4), cyg = f4c(k[5], q4);
 #pragma unroll
@@ -564,7 +582,7 @@ __device__ __forceinline__ void div_gather_chunked(
 #pragma unroll
       for (int q4 = 0; q4 < 4; ++q4) {
         float f[8];
-        ld8(FGv + (size_t)i4c(u, q4) * 8, f);
+        ld8(FGv + (size_t)chk_idx(i4c(u, q4), V, err) * 8, f);
         const float c0f = f4c(k[0], q4), c0g = f4c(k[1], q4), cxf = f4c(k[2], q4);
         const float cxg = f4c(k[3], q4), cyf = f4c(k[4], q4), cyg = f4c(k[5], q4);
 #pragma unroll
@@ -585,7 +603,7 @@ __device__ __forceinline__ void div_gather_chunked(
 #pragma unroll
     for (int q4 = 0; q4 < 4; ++q4) {
       float hv[4];
-      ld4(h + (size_t)i4c(e, q4) * 4, hv);
+      ld4(h + (size_t)chk_idx(i4c(e, q4), Ef, err) * 4, hv);
       const float a0 = f4c(d0, q4), ax = f4c(dx, q4), ay = f4c(dy, q4);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -604,7 +622,7 @@ __device__ __forceinline__ bool finite_bits(double x) {
 }
 
 template <typename T, int G, bool VISC>
-__device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __restrict__ vptr,
+__device__ __forceinline__ void div_body(int gt, int A, int V, int Ef, const int32_t* __restrict__ vptr,
                                          const int32_t* __restrict__ vidx,
                                          const int32_t* __restrict__ eptr,
                                          const int32_t* __restrict__ eidx,
@@ -625,7 +643,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = T(0);
   if constexpr (std::is_same<T, float>::value) {
-    if (live) div_gather_chunked<G, VISC>(r, lane, vptr, vidx, eptr, eidx, cv, ce, cvis, FG, FGv, h, acc);
+    if (live) div_gather_chunked<G, VISC>(r, lane, V, Ef, err, vptr, vidx, eptr, eidx, cv, ce, cvis, FG, FGv, h, acc);
   } else if (live) {
     int n0 = __ldg(vptr + r), N = __ldg(vptr + r + 1) - n0;
     const T* c = cv + 6 * (size_t)n0;
@@ -654,7 +672,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
     };
     int j = lane;
     for (; j + G < N; j += 2 * G) {
-      int u0 = ld_stream(vidx + n0 + j), u1 = ld_stream(vidx + n0 + j + G);
+      int u0 = chk_idx(ld_stream(vidx + n0 + j), V, err), u1 = chk_idx(ld_stream(vidx + n0 + j + G), V, err);
       T f0[8], f1[8], g0[8], g1[8];
       ld8(FG + (size_t)u0 * 8, f0);
       ld8(FG + (size_t)u1 * 8, f1);
@@ -666,7 +684,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
       vtx(j + G, f1, g1);
     }
     if (j < N) {
-      int u0 = ld_stream(vidx + n0 + j);
+      int u0 = chk_idx(ld_stream(vidx + n0 + j), V, err);
       T f0[8], g0[8];
       ld8(FG + (size_t)u0 * 8, f0);
       if (VISC) ld8(FGv + (size_t)u0 * 8, g0);
@@ -685,7 +703,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
     };
     j = lane;
     for (; j + G < M; j += 2 * G) {
-      int e0 = ld_stream(eidx + m0 + j), e1 = ld_stream(eidx + m0 + j + G);
+      int e0 = chk_idx(ld_stream(eidx + m0 + j), Ef, err), e1 = chk_idx(ld_stream(eidx + m0 + j + G), Ef, err);
       T h0[4], h1[4];
       ld4(h + (size_t)e0 * 4, h0);
       ld4(h + (size_t)e1 * 4, h1);
@@ -693,7 +711,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, const int32_t* __
       edg(j + G, h1);
     }
     if (j < M) {
-      int e0 = ld_stream(eidx + m0 + j);
+      int e0 = chk_idx(ld_stream(eidx + m0 + j), Ef, err);
       T h0[4];
       ld4(h + (size_t)e0 * 4, h0);
       edg(j, h0);
@@ -744,7 +762,7 @@ template <>
 struct DivOcc<float> { static constexpr int kMinBlocks = 4; };
 
 template <typename T, int G, bool VISC>
-__global__ void __launch_bounds__(256, DivOcc<T>::kMinBlocks) k_div(int A, int V, const int32_t* __restrict__ vptr,
+__global__ void __launch_bounds__(256, DivOcc<T>::kMinBlocks) k_div(int A, int V, int Ef, const int32_t* __restrict__ vptr,
                                              const int32_t* __restrict__ vidx,
                                              const int32_t* __restrict__ eptr,
                                              const int32_t* __restrict__ eidx,
@@ -754,7 +772,7 @@ __global__ void __launch_bounds__(256, DivOcc<T>::kMinBlocks) k_div(int A, int V
                                              StageArgs sa, const int32_t* __restrict__ vmem,
                                              const unsigned long long* dtbits, double cfl,
                                              double* dt_last, unsigned* err) {
-  div_body<T, G, VISC>(blockIdx.x * blockDim.x + threadIdx.x, A, V, vptr, vidx, eptr, eidx, cv,
+  div_body<T, G, VISC>(blockIdx.x * blockDim.x + threadIdx.x, A, V, Ef, vptr, vidx, eptr, eidx, cv,
                        ce, cvis, FG, FGv, h, sa, vmem, dtbits, cfl, dt_last, err);
 }
 
@@ -764,9 +782,10 @@ __global__ void __launch_bounds__(256, DivOcc<T>::kMinBlocks) k_div(int A, int V
 // takes its values from the step's base state `base` (nothing to do when U is the base).
 __device__ __forceinline__ void ghost_body(int g, int Gn, int V, const int32_t* gid,
                                            const int32_t* gdonor, const int32_t* gflags, double* U,
-                                           const double* base) {
+                                           const double* base, unsigned* err) {
   if (g >= Gn) return;
-  int t = gid[g], d = gdonor[g], f = gflags[g];
+  int t = chk_idx(gid[g], V, err), d = gdonor[g], f = gflags[g];
+  if (d >= 0) d = chk_idx(d, V, err);
   if (d < 0) {
     if (base != U)
 #pragma unroll
@@ -782,8 +801,8 @@ __device__ __forceinline__ void ghost_body(int g, int Gn, int V, const int32_t* 
 }
 
 __global__ void k_ghost(int Gn, int V, const int32_t* gid, const int32_t* gdonor,
-                        const int32_t* gflags, double* U, const double* base) {
-  ghost_body(blockIdx.x * blockDim.x + threadIdx.x, Gn, V, gid, gdonor, gflags, U, base);
+                        const int32_t* gflags, double* U, const double* base, unsigned* err) {
+  ghost_body(blockIdx.x * blockDim.x + threadIdx.x, Gn, V, gid, gdonor, gflags, U, base, err);
 }
 
 // min over the active vertices of each mesh of l_min / (|u| + c) (R12), in two passes without
@@ -927,20 +946,20 @@ __global__ void __launch_bounds__(128) k_stage(KernelArgs ka, StageArgs sa, Phys
   double* U = const_cast<double*>(sa.Us);
   if (do_ghost) {
     for (int g = tid; g < ka.G; g += stride)
-      ghost_body(g, ka.G, ka.V, ka.gid, ka.gdonor, ka.gflags, U, sa.Un);
+      ghost_body(g, ka.G, ka.V, ka.gid, ka.gdonor, ka.gflags, U, sa.Un, ka.err);
     if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
   }
   for (int v = tid; v < ka.V; v += stride)
     vertex_body<T, VISC>(v, ka.V, sa.Us, (T*)ka.Ua, (T*)ka.FG, (T*)ka.FGv, ph);
   if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
   for (int e = tid; e < ka.Ef; e += stride)
-    edge_body<T>(e, ka.Ef, ka.sten, (const T*)ka.nrm, (const T*)ka.w5, (const T*)ka.w3,
-                 (const T*)ka.Ua, (T*)ka.h, ph);
+    edge_body<T>(e, ka.Ef, ka.V, ka.sten, (const T*)ka.nrm, (const T*)ka.w5, (const T*)ka.w3,
+                 (const T*)ka.Ua, (T*)ka.h, ph, ka.err);
   if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
   // every lane of a warp runs the same number of iterations (shuffles inside div_body)
   const long long total = (long long)ka.A * G;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride)
-    div_body<T, G, VISC>((int)(base + threadIdx.x), ka.A, ka.V, ka.vptr, ka.vidx, ka.eptr, ka.eidx,
+    div_body<T, G, VISC>((int)(base + threadIdx.x), ka.A, ka.V, ka.Ef, ka.vptr, ka.vidx, ka.eptr, ka.eidx,
                          (const T*)ka.cv, (const T*)ka.ce, (const T*)ka.cvis, (const T*)ka.FG,
                          (const T*)ka.FGv, (const T*)ka.h, sa, ka.vmem, ka.dtbits, ph.cfl,
                          ka.dt_last, ka.err);
@@ -963,7 +982,7 @@ KernelArgs kernel_args(const DevMesh& m) {
 
 cudaError_t launch_ghost(const DevMesh& m, double* U, const double* base, cudaStream_t s) {
   if (m.G == 0) return cudaSuccess;
-  k_ghost<<<blocks(m.G, 256), 256, 0, s>>>(m.G, m.V, m.gid, m.gdonor, m.gflags, U, base);
+  k_ghost<<<blocks(m.G, 256), 256, 0, s>>>(m.G, m.V, m.gid, m.gdonor, m.gflags, U, base, m.err);
   return cudaGetLastError();
 }
 
@@ -988,11 +1007,12 @@ cudaError_t launch_edge(const DevMesh& m, const Phys& ph, cudaStream_t s) {
   if (m.Ef == 0) return cudaSuccess;
   int nb = blocks(m.Ef, 128);
   if (m.precision == 0)
-    k_edge<double><<<nb, 128, 0, s>>>(m.Ef, m.sten, (const double*)m.nrm, (const double*)m.w5,
-                                      (const double*)m.w3, (const double*)m.Ua, (double*)m.h, ph);
+    k_edge<double><<<nb, 128, 0, s>>>(m.Ef, m.V, m.sten, (const double*)m.nrm, (const double*)m.w5,
+                                      (const double*)m.w3, (const double*)m.Ua, (double*)m.h, ph,
+                                      m.err);
   else
-    k_edge<float><<<nb, 128, 0, s>>>(m.Ef, m.sten, (const float*)m.nrm, (const float*)m.w5,
-                                     (const float*)m.w3, (const float*)m.Ua, (float*)m.h, ph);
+    k_edge<float><<<nb, 128, 0, s>>>(m.Ef, m.V, m.sten, (const float*)m.nrm, (const float*)m.w5,
+                                     (const float*)m.w3, (const float*)m.Ua, (float*)m.h, ph, m.err);
   return cudaGetLastError();
 }
 
@@ -1001,12 +1021,12 @@ static void div_dispatch(const DevMesh& m, const StageArgs& sa, const Phys& ph, 
   long long threads = (long long)m.A * G;
   int nb = blocks(threads, 256);
   if (m.viscous)
-    k_div<T, G, true><<<nb, 256, 0, s>>>(m.A, m.V, m.vptr, m.vidx, m.eptr, m.eidx, (const T*)m.cv,
+    k_div<T, G, true><<<nb, 256, 0, s>>>(m.A, m.V, m.Ef, m.vptr, m.vidx, m.eptr, m.eidx, (const T*)m.cv,
                                          (const T*)m.ce, (const T*)m.cvis, (const T*)m.FG,
                                          (const T*)m.FGv, (const T*)m.h, sa, m.vmem, m.dtbits,
                                          ph.cfl, m.dt_last, m.err);
   else
-    k_div<T, G, false><<<nb, 256, 0, s>>>(m.A, m.V, m.vptr, m.vidx, m.eptr, m.eidx,
+    k_div<T, G, false><<<nb, 256, 0, s>>>(m.A, m.V, m.Ef, m.vptr, m.vidx, m.eptr, m.eidx,
                                           (const T*)m.cv, (const T*)m.ce, nullptr, (const T*)m.FG,
                                           nullptr, (const T*)m.h, sa, m.vmem, m.dtbits, ph.cfl,
                                           m.dt_last, m.err);

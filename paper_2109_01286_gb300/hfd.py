@@ -10,7 +10,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libhfd.so")
+# HFD_CHECKED=1 loads the bounds-checked build (every gathered index tested on the device; an
+# index out of range is reported by check() as HFD_ERR_MESH instead of being read)
+LIB_PATH = os.path.join(_HERE, "_lib", "libhfd_check.so" if os.environ.get("HFD_CHECKED") == "1"
+                        else "libhfd.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with "

@@ -69,3 +69,42 @@ def near_threshold_vertices(m, P, U, opts, margin=1e-9):
         if bad_edges.intersection(e.tolist()):
             bad.append(P.active[r])
     return np.array(bad, dtype=np.int64)
+
+
+def checked_build_cases():
+    """Small meshes covering every gather of the forward kernels (periodic, transmissive ghosts,
+    fixed wall bands, viscous rows, a Delaunay mesh, FP32 chunks, the persistent launch):
+    name -> (mesh, state, Mesh keywords, persistent launch)."""
+    import synth
+    v = synth.jittered_grid(24, 24, 10.0, 10.0, seed=1)
+    q = synth.jittered_box_with_ghosts(24, 24, (0.0, 1.0), (0.0, 1.0), 5, seed=2)
+    t = synth.jittered_grid(16, 16, 2 * np.pi, 2 * np.pi, seed=3)
+    c = synth.couette_channel(16, 17, 6, seed=7)
+    s = synth.embedded_circle_box(16, seed=8)
+    visc_t = dict(viscous=True, mu=0.01, prandtl=0.72, R_gas=1.0 / (1.4 * 0.01))
+    visc_c = dict(viscous=True, mu=0.1, prandtl=100.0, R_gas=0.4 * 10.0 / 1.4)
+    return {
+        "vortex_fp64": (v, synth.isentropic_vortex(v), {}, False),
+        "vortex_fp32": (v, synth.isentropic_vortex(v), {"precision": "fp32"}, False),
+        "vortex_persistent": (v, synth.isentropic_vortex(v), {}, True),
+        "quad_fp64": (q, synth.four_quadrant(q), {}, False),
+        "quad_fp32": (q, synth.four_quadrant(q), {"precision": "fp32"}, False),
+        "tgv_viscous": (t, synth.taylor_green(t), visc_t, False),
+        "couette_walls": (c, synth.couette(c), visc_c, False),
+        "circular_sod": (s, synth.circular_sod(s), {}, False),
+    }
+
+
+def run_checked_build_cases(pkg, torch):
+    """Residual and two device-CFL steps of every case; raises if a mesh's error word is set."""
+    out = {}
+    for name, (m, U, kw, persistent) in checked_build_cases().items():
+        mesh = pkg.Mesh(m, **kw)
+        if persistent:
+            mesh.set_launch(True, 0)
+        X = mesh.import_state(torch.from_numpy(U).cuda())
+        out[name + "/R"] = mesh.export_state(mesh.residual(X)).cpu().numpy()
+        mesh.steps(X, 0.0, 2)
+        out[name + "/U"] = mesh.export_state(X).cpu().numpy()
+        mesh.check()
+    return out

@@ -582,3 +582,36 @@ def test_lane_setter_and_autotuner_keep_results_to_rounding(c1):
     torch.cuda.synchronize()
     mesh.check()
     assert (torch.linalg.norm(a - b) / torch.linalg.norm(a)).item() < 1e-12
+
+
+def test_bounds_checked_build_runs_clean_and_matches(tmp_path):
+    """The bounds-checked library (HFD_CHECKED=1: every gathered index of the forward kernels
+    tested on the device) runs the residual and two steps of meshes covering every gather with
+    a clean error word, and gives the normal build's results."""
+    import json
+    import os
+    import subprocess
+    import sys
+    from gpu_helpers import run_checked_build_cases
+    pkg = _hfd()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = tmp_path / "checked.npz"
+    code = (
+        "import sys, numpy as np, torch\n"
+        f"sys.path[:0] = [{root!r}, {os.path.join(root, 'tests')!r}]\n"
+        "import paper_2109_01286_gb300 as pkg\n"
+        "assert pkg.hfd.LIB_PATH.endswith('libhfd_check.so'), pkg.hfd.LIB_PATH\n"
+        "from gpu_helpers import run_checked_build_cases\n"
+        f"np.savez({str(out)!r}, **run_checked_build_cases(pkg, torch))\n")
+    env = dict(os.environ, HFD_CHECKED="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    ref = run_checked_build_cases(pkg, torch)
+    got = np.load(out)
+    diffs = {}
+    for k, a in ref.items():
+        b = got[k]
+        diffs[k] = float(np.abs(a - b).max() / max(np.abs(a).max(), 1e-300))
+        tol = 1e-6 if "fp32" in k else 1e-13
+        assert diffs[k] <= tol, json.dumps(diffs)

@@ -30,6 +30,28 @@ def test_library_exports_every_declared_entry_point(pkg):
     assert declared == set(pkg.hfd.EXPORTED)
 
 
+def test_bounds_checked_build_exports_the_same_entry_points(pkg):
+    """The bounds-checked library (kernels built with -DHFD_CHECK=1) is built beside the normal
+    one and exports every entry point of include/hfd.h."""
+    import ctypes
+    path = os.path.join(os.path.dirname(pkg.hfd.__file__), "_lib", "libhfd_check.so")
+    lib = ctypes.CDLL(path)
+    for name in pkg.hfd.EXPORTED:
+        assert hasattr(lib, name), name
+
+
+def test_index_arrays_are_read_only_through_prep_set(pkg):
+    """Only coefficient arrays may be overwritten: the index streams the kernels gather through
+    stay those of the validated mesh."""
+    m = synth.jittered_grid(8, 8, 1.0, 1.0, seed=0)
+    prep = pkg.Prep(m)
+    for name in ("stencil", "flux_edges", "div_vidx", "div_eidx", "div_vptr", "div_eptr", "active",
+                 "edges"):
+        with pytest.raises(pkg.HfdError):
+            prep.set(name, prep.get(name))
+    prep.set("w5", prep.get("w5"))
+
+
 def test_default_options(pkg):
     o = pkg.options()
     assert (o.div_degree, o.visc_degree, o.precision, o.renumber) == (5, 4, 0, 1)
