@@ -532,8 +532,9 @@ def run_adjoint(args):
     area = torch.from_numpy(oracle.vertex_areas(m)).cuda()[perm]
     rho_ex = torch.from_numpy(synth.isentropic_vortex(m, beta=beta, t=T)[0]).cuda()[perm]
 
-    # The method as read amplifies perturbations exponentially, and central
-    # differences lose their meaning once the amplification swamps the step.  Horizons from the
+    # The method as read amplifies perturbations exponentially (its linearised residual has
+    # eigenvalues with positive real part on these meshes), and central differences lose their
+    # meaning once the amplification swamps the step.  Horizons from the
     # requested one downwards are checked on 4 directions, then on all directions; the longest
     # horizon whose differences agree with the adjoint to 1e-5 on every direction is used.
     requested = nsteps

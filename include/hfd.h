@@ -249,7 +249,7 @@ hfd_status hfd_steps_profiled(hfd_mesh* mesh, double* U, double dt, int32_t nste
  * HFD_ERR_ARG (sizes, null pointers, mesh not on the current device), HFD_ERR_CUDA. */
 hfd_status hfd_residual_static(hfd_mesh* mesh, double* U, double* R, void* stream);
 
-/* Discrete adjoint of one step (SURVEY config: gradients through the time stepping): given
+/* Discrete adjoint of one step (gradients through the time stepping): given
  * lam_np1 = dJ/dU_{n+1}, writes lam_n = (d hfd_step(U_n, dt) / d U_n)^T lam_np1, the exact
  * vector-Jacobian product of the discrete step (Sec. 2.3: Alg. 1, Riemann flux, least-squares
  * divergence, three-stage TVD Runge-Kutta) with the branch decisions of the sensor held fixed.
@@ -257,8 +257,11 @@ hfd_status hfd_residual_static(hfd_mesh* mesh, double* U, double* R, void* strea
  * divergence and stencil transposes are gathers over lists built on the first call, so the
  * result is deterministic.  All arrays are 12*nv device arrays in internal order; dt > 0 is the
  * fixed step of the forward step (a step with dt <= 0 depends on U_n through the CFL minimum,
- * which this product does not differentiate).  FP64 meshes without ghost vertices or
- * viscosity; other meshes get HFD_ERR_UNSUPPORTED.  Errors: HFD_ERR_ARG, HFD_ERR_CUDA. */
+ * which this product does not differentiate).  Ghost layers enter transposed: a transmissive
+ * ghost's sensitivity goes to its donor (without the derivative rows the refresh zeroes) and
+ * its column of lam_n is zero; a fixed ghost (donor -1) is an input of every stage, and its
+ * column of lam_n holds that sensitivity.  FP64 inviscid single meshes with the Roe flux; other
+ * meshes get HFD_ERR_UNSUPPORTED.  Errors: HFD_ERR_ARG, HFD_ERR_CUDA. */
 hfd_status hfd_adjoint(hfd_mesh* mesh, const double* U_n, const double* lam_np1, double* lam_n,
                        double dt, void* stream);
 

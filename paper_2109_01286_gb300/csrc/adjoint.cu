@@ -9,7 +9,15 @@
 // k_adj_edge recomputes Alg. 1 and the Roe flux of its edge (the same arithmetic and branch
 // decisions as k_edge) and runs them in reverse.  The three stages of the step are recomputed
 // forward from U_n, then reversed (Sec. 2.3 end: u1 = u + dt R(u), u2 = 3/4 u + 1/4 (u1 + dt
-// R(u1)), u+ = 1/3 u + 2/3 (u2 + dt R(u2))).  FP64 meshes without ghosts or viscosity.
+// R(u1)), u+ = 1/3 u + 2/3 (u2 + dt R(u2))).  FP64 inviscid meshes with the Roe flux.
+//
+// Ghost layers (R14) enter through the transpose T of the ghost refresh: a transmissive
+// ghost's sensitivity goes to its donor (without the derivative rows the refresh zeroes) and
+// its column becomes zero; a fixed ghost (wall band, donor -1) keeps its sensitivity, because
+// every stage state holds the step input's band values.  T is applied to lambda_{n+1} (the
+// step ends with a refresh) and to every residual product (each stage starts with one).  The
+// stage recurrences below then hold column by column: for a band column the SSP-RK3 weights
+// of each level sum to one, which gives lambda_{n+1} plus each stage's residual product.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -451,6 +459,31 @@ __global__ void __launch_bounds__(128) k_adj_vertex(
   }
 }
 
+// Transpose of the transmissive ghost refresh, in place (see the header comment): one thread
+// per donor adds its ghosts' columns, in ascending ghost order, and zeroes them.  Donors are
+// non-ghost vertices, so no column is both read as a ghost and written as a donor.
+__global__ void __launch_bounds__(128) k_adj_ghost_T(int nd, int V, const int32_t* __restrict__ donor,
+                                                     const int32_t* __restrict__ ptr,
+                                                     const int32_t* __restrict__ ghost,
+                                                     const int32_t* __restrict__ flags,
+                                                     double* lam) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  const int dn = donor[i];
+  double acc[12];
+  for (int r = 0; r < 12; ++r) acc[r] = lam[(size_t)r * V + dn];
+  for (int t = ptr[i]; t < ptr[i + 1]; ++t) {
+    const int g = ghost[t], f = flags[t];
+    for (int r = 0; r < 12; ++r) {
+      const size_t k = (size_t)r * V + g;
+      const bool zeroed = (r >= 4 && r < 8 && (f & 1)) || (r >= 8 && (f & 2));
+      if (!zeroed) acc[r] += lam[k];
+      lam[k] = 0.0;
+    }
+  }
+  for (int r = 0; r < 12; ++r) lam[(size_t)r * V + dn] = acc[r];
+}
+
 }  // namespace hfd
 
 // ------------------------------------------------------------------ host driver
@@ -538,6 +571,42 @@ hfd_status build_transposes(hfd_mesh* m) {
   izeros.assign(1, 0);
   if ((st = upload_vec(m, &m->adj_count, izeros)) != HFD_OK) return st;
   if ((st = upload_vec(m, &m->adj_B2, zeros)) != HFD_OK) return st;
+  if (d.G > 0) {
+    // donors of the transmissive ghosts, each with its ghosts in ascending internal order
+    auto gid = download(d.gid, d.G), gdn = download(d.gdonor, d.G), gfl = download(d.gflags, d.G);
+    std::vector<int> order;
+    for (int g = 0; g < d.G; ++g)
+      if (gdn[g] >= 0) order.push_back(g);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+      return gdn[a] != gdn[b] ? gdn[a] < gdn[b] : gid[a] < gid[b];
+    });
+    std::vector<int32_t> dlist, dptr(1, 0), glist, flist;
+    for (size_t i = 0; i < order.size(); ++i) {
+      int g = order[i];
+      if (dlist.empty() || dlist.back() != gdn[g]) {
+        if (!dlist.empty()) dptr.push_back((int32_t)glist.size());
+        dlist.push_back(gdn[g]);
+      }
+      glist.push_back(gid[g]);
+      flist.push_back(gfl[g]);
+    }
+    if (!dlist.empty()) dptr.push_back((int32_t)glist.size());
+    m->adj_ndonor = (int32_t)dlist.size();
+    if ((st = upload_vec(m, &m->adj_gt_donor, dlist)) != HFD_OK) return st;
+    if ((st = upload_vec(m, &m->adj_gt_ptr, dptr)) != HFD_OK) return st;
+    if ((st = upload_vec(m, &m->adj_gt_ghost, glist)) != HFD_OK) return st;
+    if ((st = upload_vec(m, &m->adj_gt_flags, flist)) != HFD_OK) return st;
+    if ((st = upload_vec(m, &m->adj_U0, zeros)) != HFD_OK) return st;
+    if ((st = upload_vec(m, &m->adj_L, zeros)) != HFD_OK) return st;
+  }
+  return HFD_OK;
+}
+
+hfd_status ghost_transpose(hfd_mesh* m, double* lam, cudaStream_t s) {
+  if (m->adj_ndonor == 0) return HFD_OK;
+  hfd::k_adj_ghost_T<<<(m->adj_ndonor + 127) / 128, 128, 0, s>>>(
+      m->adj_ndonor, m->dm.V, m->adj_gt_donor, m->adj_gt_ptr, m->adj_gt_ghost, m->adj_gt_flags, lam);
+  ACK(cudaGetLastError());
   return HFD_OK;
 }
 
@@ -563,7 +632,9 @@ hfd_status residual_vjp(hfd_mesh* m, const double* Us, const double* mu, double*
       d.V, Us, d.vptr, (const double*)d.cv, m->adj_tv_ptr, m->adj_tv_row, m->adj_tv_pos,
       m->adj_ts_ptr, m->adj_ts_ent, mu, m->adj_Ge, out, cx, X, cy, Y, cz, Z, cg, m->ph);
   ACK(cudaGetLastError());
-  return HFD_OK;
+  // X, Y, Z are transposed already (zero transmissive ghost columns), so T(out) = cx X + cy Y +
+  // cz Z + cg T((dR/dU)^T mu)
+  return ghost_transpose(m, out, s);
 }
 
 }  // namespace
@@ -576,8 +647,8 @@ extern "C" hfd_status hfd_adjoint(hfd_mesh* m, const double* U_n, const double* 
   }
   hfd::NvtxRange range("hfd_adjoint");
   const hfd::DevMesh& d = m->dm;
-  if (d.precision != 0 || d.viscous || d.G != 0 || d.nmember != 1 || m->ph.flux != 0) {
-    set_error("hfd_adjoint: built for FP64 inviscid single meshes without ghosts, Roe flux");
+  if (d.precision != 0 || d.viscous || d.nmember != 1 || m->ph.flux != 0) {
+    set_error("hfd_adjoint: built for FP64 inviscid single meshes with the Roe flux");
     return HFD_ERR_UNSUPPORTED;
   }
   if (!m->adj_Ge) {
@@ -585,22 +656,37 @@ extern "C" hfd_status hfd_adjoint(hfd_mesh* m, const double* U_n, const double* 
     if (st != HFD_OK) return st;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  double* U = const_cast<double*>(U_n);               // read only: no ghost columns to refresh
+  const size_t bytes = (size_t)12 * d.V * sizeof(double);
+  double* U = const_cast<double*>(U_n);               // read only when there are no ghosts
+  const double* lam = lam_np1;
+  if (d.G) {
+    // the caller's arrays stay untouched: the step input with refreshed ghosts, and T lam
+    ACK(cudaMemcpyAsync(m->adj_U0, U_n, bytes, cudaMemcpyDeviceToDevice, s));
+    ACK(hfd::launch_ghost(d, m->adj_U0, m->adj_U0, s));
+    U = m->adj_U0;
+    ACK(cudaMemcpyAsync(m->adj_L, lam_np1, bytes, cudaMemcpyDeviceToDevice, s));
+    hfd_status st = ghost_transpose(m, m->adj_L, s);
+    if (st != HFD_OK) return st;
+    lam = m->adj_L;
+  }
   double *u1 = m->U1, *u2 = m->U2, *B1 = m->adj_B1, *B2 = m->adj_B2;
-  // forward: the first two stage states
+  // forward: the first two stage states, each with its ghosts refreshed as the next stage
+  // of the step refreshes them (fixed ghosts from the step input)
   ACK(hfd::launch_vertex(d, U, m->ph, s));
   ACK(hfd::launch_edge(d, m->ph, s));
   ACK(hfd::launch_div(d, U, U, u1, hfd::DIV_STAGE, 0.0, 1.0, dt, m->ph, m->lanes, s));
+  if (d.G) ACK(hfd::launch_ghost(d, u1, U, s));
   ACK(hfd::launch_vertex(d, u1, m->ph, s));
   ACK(hfd::launch_edge(d, m->ph, s));
   ACK(hfd::launch_div(d, u1, U, u2, hfd::DIV_STAGE, 0.75, 0.25, dt, m->ph, m->lanes, s));
+  if (d.G) ACK(hfd::launch_ghost(d, u2, U, s));
   // reverse: lambda_u2 = 2/3 (lam + dt J(u2)^T lam)
-  hfd_status st = residual_vjp(m, u2, lam_np1, B2, 2.0 / 3.0, lam_np1, 0, nullptr, 0, nullptr,
+  hfd_status st = residual_vjp(m, u2, lam, B2, 2.0 / 3.0, lam, 0, nullptr, 0, nullptr,
                                2.0 / 3.0 * dt, s);
   if (st != HFD_OK) return st;
   // lambda_u1 = 1/4 (lambda_u2 + dt J(u1)^T lambda_u2)
   st = residual_vjp(m, u1, B2, B1, 0.25, B2, 0, nullptr, 0, nullptr, 0.25 * dt, s);
   if (st != HFD_OK) return st;
   // lambda_n = 1/3 lam + 3/4 lambda_u2 + lambda_u1 + dt J(u)^T lambda_u1
-  return residual_vjp(m, U, B1, lam_n, 1.0, B1, 1.0 / 3.0, lam_np1, 0.75, B2, dt, s);
+  return residual_vjp(m, U, B1, lam_n, 1.0, B1, 1.0 / 3.0, lam, 0.75, B2, dt, s);
 }

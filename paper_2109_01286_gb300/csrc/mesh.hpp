@@ -53,6 +53,13 @@ struct hfd_mesh {
   int32_t *adj_ts_ptr = nullptr, *adj_ts_ent = nullptr;
   double *adj_Ge = nullptr, *adj_B1 = nullptr, *adj_B2 = nullptr;
   int32_t *adj_list = nullptr, *adj_count = nullptr;
+  // transpose of the transmissive ghost refresh (meshes with ghosts): unique donors, the CSR of
+  // each donor's ghosts in ascending order with their flags; scratch for the step input with
+  // refreshed ghosts and for the transposed lambda_{n+1}
+  int32_t adj_ndonor = 0;
+  int32_t *adj_gt_donor = nullptr, *adj_gt_ptr = nullptr, *adj_gt_ghost = nullptr,
+          *adj_gt_flags = nullptr;
+  double *adj_U0 = nullptr, *adj_L = nullptr;
 };
 
 // A device block of the mesh: from the caller's allocator (hfd_options.dev_alloc) if there is
