@@ -9,7 +9,9 @@
 // k_adj_edge recomputes Alg. 1 and the Roe flux of its edge (the same arithmetic and branch
 // decisions as k_edge) and runs them in reverse.  The three stages of the step are recomputed
 // forward from U_n, then reversed (Sec. 2.3 end: u1 = u + dt R(u), u2 = 3/4 u + 1/4 (u1 + dt
-// R(u1)), u+ = 1/3 u + 2/3 (u2 + dt R(u2))).  FP64 inviscid meshes with the Roe flux.
+// R(u1)), u+ = 1/3 u + 2/3 (u2 + dt R(u2))).  FP64 meshes with the Roe flux; on viscous meshes
+// the residual adds Dv [Fv, Gv] (vertex-only rows), whose transpose k_adj_vertex gathers over
+// the same lists as the vertex part of D.
 //
 // Ghost layers (R14) enter through the transpose T of the ghost refresh: a transmissive
 // ghost's sensitivity goes to its donor (without the derivative rows the refresh zeroes) and
@@ -418,7 +420,8 @@ __global__ void __launch_bounds__(128) k_adj_edge_full(
 // stencils this vertex belongs to, then out = cx X + cy Y + cz Z + cg g.
 __global__ void __launch_bounds__(128) k_adj_vertex(
     int V, const double* __restrict__ Us, const int32_t* __restrict__ vptr,
-    const double* __restrict__ cv, const int32_t* __restrict__ tv_ptr,
+    const double* __restrict__ cv, const double* __restrict__ cvis,
+    const int32_t* __restrict__ tv_ptr,
     const int32_t* __restrict__ tv_row, const int32_t* __restrict__ tv_pos,
     const int32_t* __restrict__ ts_ptr, const int32_t* __restrict__ ts_ent,
     const double* __restrict__ mu, const double* __restrict__ Ge, double* out, double cx,
@@ -426,7 +429,9 @@ __global__ void __launch_bounds__(128) k_adj_vertex(
     Phys ph) {
   int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= V) return;
+  // R = -D [F, G, h] + Dv [Fv, Gv]: the Euler fluxes take -D^T mu, the viscous ones +Dv^T mu
   double Fb[4] = {0, 0, 0, 0}, Gb[4] = {0, 0, 0, 0};
+  double Fvb[4] = {0, 0, 0, 0}, Gvb[4] = {0, 0, 0, 0};
   for (int t = tv_ptr[u]; t < tv_ptr[u + 1]; ++t) {
     int r = tv_row[t], j = tv_pos[t];
     int n0 = vptr[r], N = vptr[r + 1] - n0;
@@ -439,11 +444,23 @@ __global__ void __launch_bounds__(128) k_adj_vertex(
       Fb[q] -= d0f * m0 + dxf * mx + dyf * my;
       Gb[q] -= d0g * m0 + dxg * mx + dyg * my;
     }
+    if (cvis) {
+      const double* z = cvis + 6 * (size_t)n0;
+      double e0f = z[j], e0g = z[N + j], exf = z[2 * N + j], exg = z[3 * N + j];
+      double eyf = z[4 * N + j], eyg = z[5 * N + j];
+      for (int q = 0; q < 4; ++q) {
+        double m0 = mu[(size_t)q * V + r], mx = mu[(size_t)(4 + q) * V + r];
+        double my = mu[(size_t)(8 + q) * V + r];
+        Fvb[q] += e0f * m0 + exf * mx + eyf * my;
+        Gvb[q] += e0g * m0 + exg * mx + eyg * my;
+      }
+    }
   }
-  double w[4], g[12];
-  for (int r = 0; r < 4; ++r) w[r] = Us[(size_t)r * V + u];
+  double w[12], g[12];
+  for (int r = 0; r < 12; ++r) w[r] = Us[(size_t)r * V + u];
   for (int r = 0; r < 12; ++r) g[r] = 0.0;
   adj::euler_flux_vjp(w, ph.gamma - 1.0, Fb, Gb, g);
+  if (cvis) adj::viscous_flux_vjp(w, ph.gamma - 1.0, ph.mu, ph.kappa, ph.R_gas, Fvb, Gvb, g);
   for (int t = ts_ptr[u]; t < ts_ptr[u + 1]; ++t) {
     int ent = ts_ent[t];
     const double* ge = Ge + (size_t)(ent / 6) * 72 + 12 * (ent % 6);
@@ -629,7 +646,8 @@ hfd_status residual_vjp(hfd_mesh* m, const double* Us, const double* mu, double*
       m->adj_te_pos, mu, m->adj_Ge, m->ph, m->adj_list, m->adj_count);
   ACK(cudaGetLastError());
   hfd::k_adj_vertex<<<(d.V + 127) / 128, 128, 0, s>>>(
-      d.V, Us, d.vptr, (const double*)d.cv, m->adj_tv_ptr, m->adj_tv_row, m->adj_tv_pos,
+      d.V, Us, d.vptr, (const double*)d.cv, d.viscous ? (const double*)d.cvis : nullptr,
+      m->adj_tv_ptr, m->adj_tv_row, m->adj_tv_pos,
       m->adj_ts_ptr, m->adj_ts_ent, mu, m->adj_Ge, out, cx, X, cy, Y, cz, Z, cg, m->ph);
   ACK(cudaGetLastError());
   // X, Y, Z are transposed already (zero transmissive ghost columns), so T(out) = cx X + cy Y +
@@ -647,8 +665,8 @@ extern "C" hfd_status hfd_adjoint(hfd_mesh* m, const double* U_n, const double* 
   }
   hfd::NvtxRange range("hfd_adjoint");
   const hfd::DevMesh& d = m->dm;
-  if (d.precision != 0 || d.viscous || d.nmember != 1 || m->ph.flux != 0) {
-    set_error("hfd_adjoint: built for FP64 inviscid single meshes with the Roe flux");
+  if (d.precision != 0 || d.nmember != 1 || m->ph.flux != 0) {
+    set_error("hfd_adjoint: built for FP64 single meshes with the Roe flux");
     return HFD_ERR_UNSUPPORTED;
   }
   if (!m->adj_Ge) {

@@ -219,5 +219,76 @@ __device__ __forceinline__ void euler_flux_vjp(const double* w, double g1, const
   prim_vjp(w, ir, u, v, p, ub, vb, pb, 0.0, 0.0, g1, wb);
 }
 
+// adjoint of the viscous fluxes Fv(w), Gv(w) at a vertex (the vertex_body chain: primitive
+// gradients by the chain rule, Stokes stresses with constant mu, Fourier heat flux with
+// p = rho R T): wbar (12 values: w, w_x, w_y) += J_Fv^T Fb + J_Gv^T Gb, in reverse order of
+// the forward statements
+__device__ __forceinline__ void viscous_flux_vjp(const double* w, double gm, double mu,
+                                                 double kappa, double R, const double* Fb,
+                                                 const double* Gb, double* wb) {
+  // forward
+  const double rho = w[0], ir = 1.0 / rho, u = w[1] * ir, v = w[2] * ir;
+  const double ux = (w[5] - u * w[4]) * ir, vx = (w[6] - v * w[4]) * ir;
+  const double uy = (w[9] - u * w[8]) * ir, vy = (w[10] - v * w[8]) * ir;
+  const double q2 = u * u + v * v;
+  const double pp = gm * (w[3] - 0.5 * rho * q2);
+  const double px = gm * (w[7] - 0.5 * w[4] * q2 - rho * (u * ux + v * vx));
+  const double py = gm * (w[11] - 0.5 * w[8] * q2 - rho * (u * uy + v * vy));
+  const double txx = mu * (4.0 / 3.0 * ux - 2.0 / 3.0 * vy);
+  const double tyy = mu * (4.0 / 3.0 * vy - 2.0 / 3.0 * ux);
+  const double txy = mu * (uy + vx);
+  // Fv = (0, txx, txy, u txx + v txy + kappa Tx), Gv = (0, txy, tyy, u txy + v tyy + kappa Ty)
+  const double btxx = Fb[1] + Fb[3] * u, btyy = Gb[2] + Gb[3] * v;
+  const double btxy = Fb[2] + Fb[3] * v + Gb[1] + Gb[3] * u;
+  double bu = Fb[3] * txx + Gb[3] * txy, bv = Fb[3] * txy + Gb[3] * tyy;
+  const double bTx = Fb[3] * kappa, bTy = Gb[3] * kappa;
+  double bux = mu * (4.0 / 3.0 * btxx - 2.0 / 3.0 * btyy);
+  double bvy = mu * (4.0 / 3.0 * btyy - 2.0 / 3.0 * btxx);
+  double buy = mu * btxy, bvx = mu * btxy;
+  // Tx = (px / rho - pp w4 / rho^2) / R, Ty likewise with py, w8
+  const double iR = 1.0 / R, ir2 = ir * ir;
+  const double bpx = bTx * iR * ir, bpy = bTy * iR * ir;
+  const double bpp = -(bTx * w[4] + bTy * w[8]) * iR * ir2;
+  double brho = bTx * iR * (-px * ir2 + 2.0 * pp * w[4] * ir2 * ir) +
+                bTy * iR * (-py * ir2 + 2.0 * pp * w[8] * ir2 * ir);
+  wb[4] -= bTx * pp * iR * ir2;
+  wb[8] -= bTy * pp * iR * ir2;
+  // px = gm (w7 - w4 q2 / 2 - rho (u ux + v vx)), py likewise
+  double bq2 = -0.5 * gm * (w[4] * bpx + w[8] * bpy);
+  wb[7] += gm * bpx;
+  wb[11] += gm * bpy;
+  wb[4] -= 0.5 * gm * q2 * bpx;
+  wb[8] -= 0.5 * gm * q2 * bpy;
+  brho -= gm * ((u * ux + v * vx) * bpx + (u * uy + v * vy) * bpy);
+  bu -= gm * rho * (ux * bpx + uy * bpy);
+  bv -= gm * rho * (vx * bpx + vy * bpy);
+  bux -= gm * rho * u * bpx;
+  bvx -= gm * rho * v * bpx;
+  buy -= gm * rho * u * bpy;
+  bvy -= gm * rho * v * bpy;
+  // pp = gm (w3 - rho q2 / 2)
+  wb[3] += gm * bpp;
+  brho -= 0.5 * gm * q2 * bpp;
+  bq2 -= 0.5 * gm * rho * bpp;
+  // q2 = u^2 + v^2
+  bu += 2.0 * u * bq2;
+  bv += 2.0 * v * bq2;
+  // ux = (w5 - u w4) / rho, vx = (w6 - v w4) / rho, uy = (w9 - u w8) / rho, vy = (w10 - v w8) / rho
+  wb[5] += bux * ir;
+  wb[6] += bvx * ir;
+  wb[9] += buy * ir;
+  wb[10] += bvy * ir;
+  wb[4] -= (u * bux + v * bvx) * ir;
+  wb[8] -= (u * buy + v * bvy) * ir;
+  bu -= (w[4] * bux + w[8] * buy) * ir;
+  bv -= (w[4] * bvx + w[8] * bvy) * ir;
+  brho -= (ux * bux + vx * bvx + uy * buy + vy * bvy) * ir;
+  // u = w1 / rho, v = w2 / rho
+  wb[1] += bu * ir;
+  wb[2] += bv * ir;
+  brho -= (u * bu + v * bv) * ir;
+  wb[0] += brho;
+}
+
 }  // namespace adj
 }  // namespace hfd
