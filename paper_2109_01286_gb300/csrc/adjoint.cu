@@ -9,7 +9,7 @@
 // k_adj_edge recomputes Alg. 1 and the Roe flux of its edge (the same arithmetic and branch
 // decisions as k_edge) and runs them in reverse.  The three stages of the step are recomputed
 // forward from U_n, then reversed (Sec. 2.3 end: u1 = u + dt R(u), u2 = 3/4 u + 1/4 (u1 + dt
-// R(u1)), u+ = 1/3 u + 2/3 (u2 + dt R(u2))).  FP64 meshes with the Roe flux; on viscous meshes
+// R(u1)), u+ = 1/3 u + 2/3 (u2 + dt R(u2))).  FP64 meshes, Roe or Rusanov flux; on viscous meshes
 // the residual adds Dv [Fv, Gv] (vertex-only rows), whose transpose k_adj_vertex gathers over
 // the same lists as the vertex part of D.
 //
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(128, 3) k_adj_edge(
     wr[r] = fb1 ? wj[r] : W5[1][r];
   }
   double b0[4] = {0, 0, 0, 0}, b1[4] = {0, 0, 0, 0};
-  adj::roe_flux_vjp(wl, wr, nx, ny, g1, ph.harten, hb, b0, b1);
+  adj::riemann_flux_vjp(wl, wr, nx, ny, ph, hb, b0, b1);
   double wib[4] = {0, 0, 0, 0}, wjb[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(128) k_adj_edge_full(
   // ---- reverse
   double wsb[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   double wib[4] = {0, 0, 0, 0}, wjb[4] = {0, 0, 0, 0};
-  adj::roe_flux_vjp(wside[0], wside[1], nx, ny, g1, ph.harten, hb, wsb[0], wsb[1]);
+  adj::riemann_flux_vjp(wside[0], wside[1], nx, ny, ph, hb, wsb[0], wsb[1]);
   if (fb[0]) { for (int r = 0; r < 4; ++r) { wib[r] += wsb[0][r]; wsb[0][r] = 0; } }
   if (fb[1]) { for (int r = 0; r < 4; ++r) { wjb[r] += wsb[1][r]; wsb[1][r] = 0; } }
   double ub = 0, vb = 0, Hb = 0, cb = 0;
@@ -665,8 +665,8 @@ extern "C" hfd_status hfd_adjoint(hfd_mesh* m, const double* U_n, const double* 
   }
   hfd::NvtxRange range("hfd_adjoint");
   const hfd::DevMesh& d = m->dm;
-  if (d.precision != 0 || d.nmember != 1 || m->ph.flux != 0) {
-    set_error("hfd_adjoint: built for FP64 single meshes with the Roe flux");
+  if (d.precision != 0 || d.nmember != 1) {
+    set_error("hfd_adjoint: built for FP64 single meshes");
     return HFD_ERR_UNSUPPORTED;
   }
   if (!m->adj_Ge) {

@@ -3,6 +3,8 @@
 // same arithmetic as the forward functions in kernels.cu (branch decisions held fixed).
 #pragma once
 
+#include "kernels.hpp"
+
 namespace hfd {
 namespace adj {
 
@@ -199,6 +201,59 @@ __device__ void roe_flux_vjp(const double* wl, const double* wr, double nx, doub
     prim_vjp(w, ir, uk, vk, pk, nx * unb, ny * unb, pb, 0.0, 0.0, g1, wbx);
   }
   roe_state_vjp(wl, wr, g1, s, ub, vb, Hb, cb, wlb, wrb);
+}
+
+// adjoint of one side of Rusanov's flux: the normal flux f(w) = (rho u_n, m u_n + p n_x,
+// n u_n + p n_y, (E + p) u_n) with bar fb, and the side's speed |u_n| + c with bar sb
+__device__ __forceinline__ void rusanov_side_vjp(const double* w, double nx, double ny, double g1,
+                                                 const double* fb, double sb, double* wb) {
+  const double ir = 1.0 / w[0], u = w[1] * ir, v = w[2] * ir;
+  const double p = g1 * (w[3] - 0.5 * (w[1] * u + w[2] * v));
+  const double un = u * nx + v * ny, gam = g1 + 1.0;
+  const double c = sqrt(gam * p * ir);
+  const double unb = fb[0] * w[0] + fb[1] * w[1] + fb[2] * w[2] + fb[3] * (w[3] + p) +
+                     (un < 0.0 ? -sb : sb);
+  const double pb = fb[1] * nx + fb[2] * ny + fb[3] * un + sb * gam * ir / (2.0 * c);
+  const double irb = sb * gam * p / (2.0 * c);
+  wb[0] += fb[0] * un;
+  wb[1] += fb[1] * un;
+  wb[2] += fb[2] * un;
+  wb[3] += fb[3] * un;
+  prim_vjp(w, ir, u, v, p, nx * unb, ny * unb, pb, 0.0, irb, g1, wb);
+}
+
+// adjoint of Rusanov's flux h = (f(wl) + f(wr)) / 2 - s (wr - wl) / 2, s = max of the two sides'
+// |u_n| + c (kernels.cu: rusanov_flux; the larger side takes the bar, the left one on a tie)
+__device__ __forceinline__ void rusanov_flux_vjp(const double* wl, const double* wr, double nx,
+                                                 double ny, double g1, const double* hb,
+                                                 double* wlb, double* wrb) {
+  auto speed = [&](const double* w) {
+    const double ir = 1.0 / w[0];
+    const double un = (w[1] * nx + w[2] * ny) * ir;
+    const double p = g1 * (w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) * ir);
+    return fabs(un) + sqrt((g1 + 1.0) * p * ir);
+  };
+  const double sl = speed(wl), sr = speed(wr);
+  const double s = sl >= sr ? sl : sr;
+  double sbar = 0.0, fb[4];
+  for (int i = 0; i < 4; ++i) {
+    fb[i] = 0.5 * hb[i];
+    sbar -= 0.5 * hb[i] * (wr[i] - wl[i]);
+    wlb[i] += 0.5 * s * hb[i];
+    wrb[i] -= 0.5 * s * hb[i];
+  }
+  rusanov_side_vjp(wl, nx, ny, g1, fb, sl >= sr ? sbar : 0.0, wlb);
+  rusanov_side_vjp(wr, nx, ny, g1, fb, sl >= sr ? 0.0 : sbar, wrb);
+}
+
+// adjoint of the edge's numerical flux with the solver the mesh was built with
+__device__ __forceinline__ void riemann_flux_vjp(const double* wl, const double* wr, double nx,
+                                                 double ny, const Phys& ph, const double* hb,
+                                                 double* wlb, double* wrb) {
+  if (ph.flux == 1)
+    rusanov_flux_vjp(wl, wr, nx, ny, ph.g1, hb, wlb, wrb);
+  else
+    roe_flux_vjp(wl, wr, nx, ny, ph.g1, ph.harten, hb, wlb, wrb);
 }
 
 // adjoint of the Euler fluxes F(w), G(w) at a vertex: wbar += J_F^T Fb + J_G^T Gb

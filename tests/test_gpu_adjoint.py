@@ -18,20 +18,20 @@ def _pkg():
     return pkg
 
 
-@pytest.mark.parametrize("conservative", [False, True])
-def test_adjoint_step_matches_oracle_adjoint_20x20(conservative):
+@pytest.mark.parametrize("conservative,flux", [(False, "roe"), (True, "roe"), (False, "rusanov")])
+def test_adjoint_step_matches_oracle_adjoint_20x20(conservative, flux):
     """The GPU adjoint of one step against the oracle's adjoint on a 20 x 20 vortex mesh, with
     the oracle's coefficients in both (kernel parity); also for the conservative variant, whose
-    coefficients and flux directions the same reverse kernels take."""
+    coefficients and flux directions the same reverse kernels take, and for Rusanov's flux."""
     pkg = _pkg()
     m = synth.jittered_grid(20, 20, 10.0, 10.0, seed=5)
     U = synth.isentropic_vortex(m)
-    opts = oracle.Options(conservative=conservative)
+    opts = oracle.Options(conservative=conservative, flux=flux)
     P = oracle.prepare(m, opts)
     dt = oracle.cfl_dt(m, P, U)
     lam = np.random.default_rng(0).standard_normal(U.shape)
     ref = ADJ.step_vjp(m, P, U, dt, lam, opts)
-    prep = pkg.Prep(m, conservative=conservative)
+    prep = pkg.Prep(m, conservative=conservative, flux=flux)
     inject_oracle_coefficients(prep, P, len(m["x"]))
     mesh = prep.upload()
     Ui = mesh.import_state(torch.from_numpy(U).cuda())
