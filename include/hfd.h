@@ -261,8 +261,9 @@ hfd_status hfd_residual_static(hfd_mesh* mesh, double* U, double* R, void* strea
  * ghost's sensitivity goes to its donor (without the derivative rows the refresh zeroes) and
  * its column of lam_n is zero; a fixed ghost (donor -1) is an input of every stage, and its
  * column of lam_n holds that sensitivity.  Viscous meshes add the reverse of the vertex
- * viscous fluxes and the transposed viscous rows.  Roe or Rusanov flux.  FP64 single meshes;
- * FP32 meshes and batches get HFD_ERR_UNSUPPORTED.  Errors: HFD_ERR_ARG, HFD_ERR_CUDA. */
+ * viscous fluxes and the transposed viscous rows.  Roe or Rusanov flux.  A batch
+ * (hfd_prep_concat) takes the one dt for every member, and its product is each member's.
+ * FP64 meshes; FP32 meshes get HFD_ERR_UNSUPPORTED.  Errors: HFD_ERR_ARG, HFD_ERR_CUDA. */
 hfd_status hfd_adjoint(hfd_mesh* mesh, const double* U_n, const double* lam_np1, double* lam_n,
                        double dt, void* stream);
 

@@ -50,6 +50,29 @@ def test_batch_residual_and_steps_equal_single_meshes(members):
     assert len(set(dts)) == 3
 
 
+def test_batch_adjoint_equals_single_mesh_adjoints(members):
+    """hfd_adjoint on a batch (one fixed dt for every member) gives each member's own adjoint:
+    the transposed gathers of the union mesh visit a member's rows in the member's order."""
+    pkg = _pkg()
+    preps = [pkg.Prep(x["mesh"]) for x in members]
+    batch = pkg.Prep.concat(preps).upload()
+    Ub = np.concatenate([x["U"] for x in members], axis=1)
+    rng = np.random.default_rng(3)
+    lams = [rng.standard_normal(x["U"].shape) for x in members]
+    dt = 0.01                                 # below every member's CFL step (>= 0.037)
+    Lb = batch.export_state(batch.adjoint(_state(batch, Ub), _state(batch, np.concatenate(lams, axis=1)),
+                                          dt=dt)).cpu().numpy()
+    off = 0
+    for k, x in enumerate(members):
+        single = preps[k].upload()
+        V = x["U"].shape[1]
+        L = single.export_state(single.adjoint(_state(single, x["U"]), _state(single, lams[k]),
+                                               dt=dt)).cpu().numpy()
+        err = np.abs(Lb[:, off:off + V] - L).max() / np.abs(L).max()
+        assert err < 1e-13, (k, err)
+        off += V
+
+
 def test_batch_matches_oracle_residual(members):
     pkg = _pkg()
     x = members[0]
