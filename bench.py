@@ -514,7 +514,6 @@ def run_adjoint(args):
     10 steps on which the run stays finite and 4 directions agree to 1e-5 is used.  Reports the
     cost of the backward pass relative to the forward pass."""
     import torch
-    import oracle
     from paper_2109_01286_gb300 import Mesh
     from paper_2109_01286_gb300.autograd import rollout
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -529,7 +528,7 @@ def run_adjoint(args):
     del probe
     T = nsteps * dt
     perm = torch.from_numpy(mesh.perm.astype(np.int64)).cuda()
-    area = torch.from_numpy(oracle.vertex_areas(m)).cuda()[perm]
+    area = torch.from_numpy(synth.vertex_areas(m)).cuda()[perm]
     rho_ex = torch.from_numpy(synth.isentropic_vortex(m, beta=beta, t=T)[0]).cuda()[perm]
 
     # The method as read amplifies perturbations exponentially (its linearised residual has

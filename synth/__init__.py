@@ -8,11 +8,11 @@ embedded-circle mesh, Sec. 3.3) and of the synthetic workloads (four-quadrant Ri
 problem, planar Sod, Taylor-Green vortex).
 """
 from .meshes import (jittered_grid, jittered_box_with_ghosts, couette_channel,
-                     embedded_circle_box, mesh_summary)
+                     embedded_circle_box, mesh_summary, vertex_areas)
 from .states import (GAMMA, isentropic_vortex, four_quadrant, planar_sod, taylor_green,
                      uniform_state, prim_to_cons, couette, circular_sod)
 from .workloads import batched_vortices
 
-__all__ = ["jittered_grid", "jittered_box_with_ghosts", "couette_channel", "embedded_circle_box", "mesh_summary", "GAMMA",
+__all__ = ["jittered_grid", "jittered_box_with_ghosts", "couette_channel", "embedded_circle_box", "mesh_summary", "vertex_areas", "GAMMA",
            "isentropic_vortex", "four_quadrant", "planar_sod", "taylor_green",
            "uniform_state", "prim_to_cons", "couette", "circular_sod", "batched_vortices"]

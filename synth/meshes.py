@@ -175,3 +175,22 @@ def embedded_circle_box(n, seed, radius=0.5, half=1.0, ghost=5, jitter=0.15, ban
         "ghost_flags": g["ghost_flags"], "grid": (NX, NY), "h": (h, h), "seed": seed,
         "on_circle": on_circle, "radius": radius,
     }
+
+
+def vertex_areas(mesh):
+    """Weights of an area-weighted objective over the vertices (the adjoint workload's
+    J = sum_v A_v (rho - rho_exact)^2): one third of the area of every incident triangle, with
+    triangle edges taken by the minimum image across periodic sides."""
+    x, y = np.asarray(mesh["x"]), np.asarray(mesh["y"])
+    t = np.asarray(mesh["tri"], dtype=np.int64)
+
+    def d(a, b, c, L, per):
+        v = c[b] - c[a]
+        return v - L * np.round(v / L) if per else v
+    ax, ay = d(t[:, 0], t[:, 1], x, mesh["Lx"], mesh["periodic_x"]), d(t[:, 0], t[:, 1], y, mesh["Ly"], mesh["periodic_y"])
+    bx, by = d(t[:, 0], t[:, 2], x, mesh["Lx"], mesh["periodic_x"]), d(t[:, 0], t[:, 2], y, mesh["Ly"], mesh["periodic_y"])
+    third = (0.5 * (ax * by - ay * bx)) / 3.0
+    A = np.zeros(len(x))
+    for k in range(3):
+        np.add.at(A, t[:, k], third)
+    return A

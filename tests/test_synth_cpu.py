@@ -86,3 +86,20 @@ def test_circular_sod_state(circ):
     np.testing.assert_array_equal(U[0, ~inside], 0.125)
     np.testing.assert_allclose(U[3, ~inside], 0.25, rtol=1e-15)
     assert np.all(U[1:3] == 0.0) and np.all(U[4:] == 0.0)
+
+
+@pytest.mark.parametrize("kind", ["periodic", "box", "circle"])
+def test_vertex_areas_tile_the_domain(kind):
+    """The objective weights: one third of each incident triangle; they sum to the domain area
+    (periodic triangles by the minimum image) and are positive."""
+    if kind == "periodic":
+        m, area = synth.jittered_grid(12, 9, 10.0, 7.0, seed=4), 70.0
+    elif kind == "box":
+        m, area = synth.jittered_box_with_ghosts(10, 10, (0.0, 1.0), (0.0, 2.0), 2, seed=4), None
+    else:
+        m, area = synth.embedded_circle_box(16, seed=8), None
+    A = synth.vertex_areas(m)
+    assert np.all(A > 0)
+    if area is None:
+        area = (m["x"].max() - m["x"].min()) * (m["y"].max() - m["y"].min())
+    assert abs(A.sum() - area) < 1e-12 * area
