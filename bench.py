@@ -53,11 +53,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="four-quadrant",
                     choices=["four-quadrant", "batched", "adjoint", "tgv", "conservative",
-                             "circular-sod"],
+                             "circular-sod", "vortex-order"],
                     help="batched: 256 uneven isentropic-vortex meshes advanced together; "
                          "adjoint: gradient of a 200-step vortex run, checked by differences; "
                          "conservative: the four-quadrant line with median-dual value rows; "
-                         "circular-sod: Sec. 3.3 on embedded-circle Delaunay meshes")
+                         "circular-sod: Sec. 3.3 on embedded-circle Delaunay meshes; "
+                         "vortex-order: Sec. 3.1 density error at 50-150 segments per side")
     ap.add_argument("--directions", type=int, default=64)
     ap.add_argument("--batch", type=int, default=256)
     return ap.parse_args()
@@ -720,6 +721,61 @@ def run_tgv(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ vortex accuracy workload
+def run_vortex_order(args):
+    """Accuracy test of Sec. 3.1 at the paper's resolutions: the isentropic vortex (beta 5,
+    gamma 1.4) advected by the mean flow (1, 1) on the periodic [-10, 10]^2, on meshes of 50,
+    75, 100 and 150 segments per side (jittered random-split grids standing in for the paper's
+    Delaunay meshes), FP64 SSP-RK3.  Each mesh takes a fixed step: its CFL-0.3 step rounded
+    down so that the checkpoints t = 0.25, 0.5, 1, 2 fall on steps.  Reports the area-weighted
+    L2 and the max density error against the exact translated vortex at each checkpoint and the
+    observed order between consecutive meshes."""
+    import torch
+    from paper_2109_01286_gb300 import Mesh
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    Ns, marks, quantum = (50, 75, 100, 150), (0.25, 0.5, 1.0, 2.0), 0.25
+    vortex = dict(beta=5.0, center=(0.0, 0.0), mean=(1.0, 1.0))
+    rows = []
+    for N in Ns:
+        m = synth.jittered_grid(N, N, 20.0, 20.0, seed=1, x0=-10.0, y0=-10.0)
+        mesh = Mesh(m)
+        X = mesh.import_state(torch.from_numpy(synth.isentropic_vortex(m, **vortex)).cuda())
+        probe = X.clone()
+        mesh.step(probe, 0.0)
+        dt = quantum / np.ceil(quantum / mesh.last_dt())
+        del probe
+        A = synth.vertex_areas(m)
+        done, t0 = 0, time.perf_counter()
+        errs = {}
+        for T in marks:
+            k = int(round(T / dt))
+            mesh.steps(X, dt, k - done)
+            done = k
+            rho = mesh.export_state(X)[0].cpu().numpy()
+            ex = synth.isentropic_vortex(m, t=T, **vortex)[0]
+            d = rho - ex
+            errs[T] = {"l2": float(np.sqrt(np.sum(A * d * d) / np.sum(A))),
+                       "max": float(np.abs(d).max()), "finite": bool(np.all(np.isfinite(rho)))}
+        rows.append({"segments": N, "vertices": len(m["x"]), "h": 20.0 / N, "dt": dt,
+                     "steps": done, "errors": {str(T): e for T, e in errs.items()},
+                     "wall_s": time.perf_counter() - t0})
+    orders = {}
+    for T in marks:
+        o = []
+        for a, b in zip(rows[:-1], rows[1:]):
+            ea, eb = a["errors"][str(T)]["l2"], b["errors"][str(T)]["l2"]
+            o.append(float(np.log(ea / eb) / np.log(b["segments"] / a["segments"]))
+                     if ea > 0 and eb > 0 and np.isfinite(ea) and np.isfinite(eb) else None)
+        orders[str(T)] = o
+    line = {"metric": "density error order", "workload": "vortex-order", "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "isentropic vortex beta 5, mean flow (1,1), periodic "
+                                   "[-10,10]^2, jittered random-split meshes of 50/75/100/150 "
+                                   "segments per side, FP64, CFL <= 0.3"},
+            "runs": rows, "l2_orders_between_consecutive_meshes": orders}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ circular Sod workload
 def run_circular_sod(args):
     """Circular Sod problem (Sec. 3.3) on embedded-circle Delaunay meshes of [-1, 1]^2 whose
@@ -804,6 +860,8 @@ def main():
         run_tgv(args)
     elif args.workload == "circular-sod":
         run_circular_sod(args)
+    elif args.workload == "vortex-order":
+        run_vortex_order(args)
     else:
         run_native(args)
 
