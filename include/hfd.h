@@ -105,6 +105,10 @@ typedef struct {
                               dual-face area vector of edge e, and every edge's projection and
                               Riemann flux is taken along S_e/|S_e|; the derivative rows stay
                               least squares (with edge rows along S_e)                    [0] */
+  int32_t force_branch;    /* debugging and testing aid (Alg. 1's branch taken for every
+                              characteristic component and side instead of the sensor's
+                              choice): 0 the sensor decides, 1 the 5-node Hermite value,
+                              2 the WENO-weighted 3-node candidates.  hfd_adjoint supports 0 [0] */
 } hfd_options;
 
 typedef struct {

@@ -46,6 +46,7 @@ class Options:
     harten: float = 0.1           # R9: entropy-fix width delta = harten * c_roe
     flux: str = "roe"             # R9: Riemann solver, "roe" or "rusanov"
     conservative: bool = False    # value equations as median-dual finite volumes (not in the paper)
+    force_branch: str = "sensor"  # testing aid: "hermite" / "weno" take that branch of Alg. 1 everywhere
     viscous: bool = False
     mu: float = 0.0
     prandtl: float = 0.72
@@ -620,6 +621,8 @@ def edge_values_from_stencil(P, W, opts, diag=None):
         c3 = [np.einsum("en,eqn->eq", P.w3[:, side, j], C[0][:, :, three[j]]) for j in range(3)]
         weighted = o1 * c3[0] + o2 * c3[1] + o3 * c3[2]
         smooth = (np.real(o1) > opts.sens_lo) & (np.real(o1) < opts.sens_hi)
+        if opts.force_branch != "sensor":
+            smooth = np.full(smooth.shape, {"hermite": True, "weno": False}[opts.force_branch])
         cs = np.where(smooth, c5, weighted)
         ws = np.einsum("eij,ej->ie", R, cs)          # back-projection w = R c
         if diag is not None:

@@ -665,8 +665,8 @@ extern "C" hfd_status hfd_adjoint(hfd_mesh* m, const double* U_n, const double* 
   }
   hfd::NvtxRange range("hfd_adjoint");
   const hfd::DevMesh& d = m->dm;
-  if (d.precision != 0) {
-    set_error("hfd_adjoint: built for FP64 meshes");
+  if (d.precision != 0 || m->ph.force_branch != 0) {
+    set_error("hfd_adjoint: built for FP64 meshes whose sensor decides the branch");
     return HFD_ERR_UNSUPPORTED;
   }
   if (!m->adj_Ge) {

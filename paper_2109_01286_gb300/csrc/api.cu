@@ -306,6 +306,7 @@ hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
   m->ph.R_gas = o.R_gas;
   m->ph.kappa = o.mu * (o.gamma * o.R_gas / (o.gamma - 1.0)) / o.prandtl;
   m->ph.flux = o.flux;
+  m->ph.force_branch = o.force_branch;
   m->ph.finish();
   // ---- stats
   hfd_mesh_stats& s = m->stats;

@@ -408,6 +408,8 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
       if (!(mlo > 0.f && mhi > 0.f)) rough |= bit;
       if (!(fabsf(mlo) > kGuard * S && fabsf(mhi) > kGuard * S)) amb |= bit;
     }
+  if (ph.force_branch == 1) rough = amb = 0u;                 // every side 5-node
+  else if (ph.force_branch == 2) { rough = 0xffu; amb = 0u; } // every side 3-node WENO
   T wside[2][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) { wside[0][r] = W5L[r]; wside[1][r] = W5R[r]; }
@@ -437,7 +439,7 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
         double t[3], S;
         sensor64(cq[0], cq[1], cq[2], cq[3], cq[4], ph, t, S);
         bool smooth = (t[0] > ph.sens_lo * S) && (t[0] < ph.sens_hi * S);
-        if (smooth) continue;
+        if (smooth && ph.force_branch != 2) continue;
         const T* w = w3 + (size_t)(9 * side) * Ef + e;
         T c1 = ld_stream(w) * cq[0] + ld_stream(w + Ef) * cq[1] + ld_stream(w + 2 * (size_t)Ef) * cq[2];
         T c2 = ld_stream(w + 3 * (size_t)Ef) * cq[1] + ld_stream(w + 4 * (size_t)Ef) * cq[2] +

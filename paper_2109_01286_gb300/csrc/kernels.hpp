@@ -11,6 +11,7 @@ struct Phys {
   double gamma, eps, sens_lo, sens_hi, harten, cfl;
   double mu, kappa, R_gas;      // viscous model (Sec. 2.3; constant mu, kappa = mu c_p / Pr)
   int flux;                     // 0 Roe (Harten's fix), 1 Rusanov
+  int force_branch;             // 0 sensor, 1 every side 5-node, 2 every side 3-node WENO
   double g1;                    // gamma - 1
   // the same constants rounded once to FP32 on the host (no FP64 conversions in FP32 kernels)
   float g1f, epsf, sens_lof, sens_hif, hartenf;

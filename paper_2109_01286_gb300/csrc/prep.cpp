@@ -405,7 +405,7 @@ hfd_status build_prep(const hfd_mesh_desc* d, const hfd_options* o, Prep* P) {
   if (o->div_degree < 2 || o->div_degree > 6 || o->visc_degree < 2 || o->visc_degree > 6 ||
       o->precision < 0 || o->precision > 1 || !(o->visc_coef_max > 0.0) ||
       (o->dev_alloc == nullptr) != (o->dev_free == nullptr) || o->flux < 0 || o->flux > 1 ||
-      o->conservative < 0 || o->conservative > 1) {
+      o->conservative < 0 || o->conservative > 1 || o->force_branch < 0 || o->force_branch > 2) {
     set_error("hfd_prep_create: option out of range");
     return HFD_ERR_ARG;
   }
@@ -924,7 +924,7 @@ hfd_status hfd_prep_concat(const hfd_prep* const* preps, int32_t n, hfd_prep** o
         o.R_gas != o0.R_gas || o.weno_eps != o0.weno_eps || o.sens_lo != o0.sens_lo ||
         o.sens_hi != o0.sens_hi || o.harten != o0.harten || o.cfl != o0.cfl ||
         o.precision != o0.precision || o.visc_coef_max != o0.visc_coef_max || o.flux != o0.flux ||
-        o.conservative != o0.conservative) {
+        o.conservative != o0.conservative || o.force_branch != o0.force_branch) {
       hfd::set_error("hfd_prep_concat: member %d has different physical/numerical options", k);
       return HFD_ERR_ARG;
     }

@@ -75,7 +75,7 @@ class Options(ctypes.Structure):
                 ("harten", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("visc_coef_max", ctypes.c_double), ("dev_alloc", _ALLOC_FN),
                 ("dev_free", _FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("flux", ctypes.c_int32),
-                ("conservative", ctypes.c_int32)]
+                ("conservative", ctypes.c_int32), ("force_branch", ctypes.c_int32)]
 
 
 class MeshDesc(ctypes.Structure):
@@ -144,7 +144,8 @@ def _ok(status, where):
 
 def options(**kw):
     """hfd_options with the library defaults, overridden by keyword (precision may be 'fp64' or
-    'fp32', flux 'roe' or 'rusanov'; booleans are accepted for viscous/renumber;
+    'fp32', flux 'roe' or 'rusanov', force_branch 'sensor', 'hermite' or 'weno'; booleans are
+    accepted for viscous/renumber;
     allocator='torch' takes the mesh's device memory from PyTorch's caching allocator)."""
     o = Options()
     _lib.hfd_default_options(ctypes.byref(o))
@@ -158,6 +159,8 @@ def options(**kw):
             v = {"fp64": 0, "fp32": 1, "mixed": 1}[v]
         if k == "flux" and isinstance(v, str):
             v = {"roe": 0, "rusanov": 1}[v]
+        if k == "force_branch" and isinstance(v, str):
+            v = {"sensor": 0, "hermite": 1, "weno": 2}[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
         setattr(o, k, int(v) if isinstance(v, bool) else v)

@@ -615,3 +615,34 @@ def test_bounds_checked_build_runs_clean_and_matches(tmp_path):
         diffs[k] = float(np.abs(a - b).max() / max(np.abs(a).max(), 1e-300))
         tol = 1e-6 if "fp32" in k else 1e-13
         assert diffs[k] <= tol, json.dumps(diffs)
+
+
+@pytest.mark.parametrize("case,branch,precision,tol", [
+    ("c1", "weno", "fp64", TOL_FP64), ("quad", "hermite", "fp64", TOL_FP64),
+    ("quad", "weno", "fp64", TOL_FP64), ("c1", "weno", "fp32", 1e-4)])
+def test_forced_branch_kernel_parity(case, branch, precision, tol, request):
+    """Alg. 1 with one branch forced on every characteristic component and side (a testing
+    aid): every edge of the smooth vortex through the WENO-weighted 3-node candidates, every
+    edge of the four-quadrant problem through the 5-node values or the candidates; no branch is
+    left to rounding, so no vertex is excluded."""
+    pkg = _hfd()
+    m, _, U = request.getfixturevalue(case)
+    opts = oracle.Options(force_branch=branch)
+    P = oracle.prepare(m, opts)
+    prep = pkg.Prep(m, force_branch=branch, precision=precision)
+    inject_oracle_coefficients(prep, P, len(m["x"]))
+    R = _residual(prep.upload(), U)
+    R_ref = oracle.residual(m, P, U.copy(), opts)
+    err = rel_l2_groups(R, R_ref)
+    assert max(err) < tol, err
+    assert max(rel_l2_groups(R, oracle.residual(m, oracle.prepare(m), U.copy()))) > 10 * tol
+
+
+def test_adjoint_refuses_a_forced_branch(c1):
+    pkg = _hfd()
+    m, _, U = c1
+    mesh = pkg.Mesh(m, force_branch="weno")
+    Ui = mesh.import_state(torch.from_numpy(U).cuda())
+    with pytest.raises(pkg.HfdError) as e:
+        mesh.adjoint(Ui, Ui.clone(), dt=0.01)
+    assert e.value.status == 9

@@ -185,6 +185,9 @@ def test_allocator_and_flux_options_are_checked(pkg):
     ct = pkg.hfd.ctypes
     bad = pkg.options(flux=2)
     assert pkg.hfd._lib.hfd_prep_create(ct.byref(d), ct.byref(bad), ct.byref(h)) == 1
+    assert pkg.options(force_branch="weno").force_branch == 2 and pkg.options().force_branch == 0
+    bad = pkg.options(force_branch=3)
+    assert pkg.hfd._lib.hfd_prep_create(ct.byref(d), ct.byref(bad), ct.byref(h)) == 1
     o = pkg.options(allocator="torch")
     assert bool(o.dev_alloc) and bool(o.dev_free)
     o.dev_free = pkg.hfd._FREE_FN()          # only one of the two callbacks: rejected
