@@ -646,3 +646,28 @@ def test_adjoint_refuses_a_forced_branch(c1):
     with pytest.raises(pkg.HfdError) as e:
         mesh.adjoint(Ui, Ui.clone(), dt=0.01)
     assert e.value.status == 9
+
+
+def test_circular_sod_against_radial_reference():
+    """Sec. 3.3: the CUDA path's density on the embedded-circle meshes of 24 and 50 segments
+    per side at t = 0.03 (fixed steps below CFL 0.3; the state of the method as read turns
+    inadmissible soon after) against the high-resolution 1D radial reference solution, by the
+    area-weighted L1 error over the physical vertices.  The error is that of the smeared
+    shock, contact and rarefaction, and falls with the mesh."""
+    from oracle import radial
+    pkg = _hfd()
+    T = 0.03
+    rc, (rho_ref, _, _) = radial.circular_sod(T, n=4000)
+    errs = []
+    for n, k in ((24, 5), (50, 10)):
+        m = synth.embedded_circle_box(n, seed=8)
+        mesh = pkg.Mesh(m)
+        X = mesh.import_state(torch.from_numpy(synth.circular_sod(m)).cuda())
+        mesh.steps(X, T / k, k)
+        mesh.check()
+        rho = mesh.export_state(X)[0].cpu().numpy()
+        phys = np.setdiff1d(np.arange(len(m["x"])), m["ghost_ids"])
+        A = synth.vertex_areas(m)[phys]
+        ref = np.interp(np.hypot(m["x"], m["y"])[phys], rc, rho_ref)
+        errs.append(float(np.sum(A * np.abs(rho[phys] - ref)) / np.sum(A)))
+    assert errs[0] < 0.025 and errs[1] < 0.016 and errs[1] < 0.8 * errs[0], errs

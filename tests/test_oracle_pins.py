@@ -767,3 +767,42 @@ def test_oracle_adjoint_dot_product_against_complex_step(kind):
     lhs = np.sum(mu * Sj)
     rhs = np.sum(ADJ.step_vjp(m, P, U, dt, mu, opts) * delta)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+# ------------------------------------------------------------------ radial reference (Sec. 3.3)
+
+def test_radial_reference_planar_mode_converges_to_the_exact_riemann_solution():
+    """With the geometric terms off, the reference scheme solves Sod's shock tube; its L1
+    density error against the exact solution (Toro's solver) is small and falls with the cell
+    count (first order is the best a discontinuous solution allows in L1)."""
+    from exact_riemann import sample
+    from oracle import radial
+    errs = []
+    for n in (400, 1600):
+        s = radial.Radial(n, 1.0, alpha=0)
+        x = s.rc
+        U = s.run(radial._cons(np.where(x < 0.5, 1.0, 0.125), 0 * x, np.where(x < 0.5, 1.0, 0.1),
+                               1.4), 0.2)
+        rho = radial._prim(U, 1.4)[0]
+        errs.append(np.mean(np.abs(rho - sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), (x - 0.5) / 0.2)[0])))
+    assert errs[0] < 3e-3 and errs[1] < errs[0] / 2.5, errs
+
+
+def test_radial_reference_conserves_and_keeps_rest():
+    """Cylindrical mode: total mass and energy (cell volumes r dr) are conserved to rounding
+    while no wave leaves the domain, and a fluid at rest stays exactly at rest (the pressure
+    source balances the pressure flux on every cell)."""
+    from oracle import radial
+    s = radial.Radial(400, 2.0, alpha=1)
+    inner = s.rc < 0.5
+    U0 = radial._cons(np.where(inner, 1.0, 0.125), 0 * s.rc, np.where(inner, 1.0, 0.1), 1.4)
+    U = s.run(U0, 0.2)
+    for k in (0, 2):
+        assert abs(np.sum(U[k] * s.V) - np.sum(U0[k] * s.V)) < 1e-13 * np.sum(U0[k] * s.V)
+    Ur = s.run(radial._cons(1.0 + 0 * s.rc, 0 * s.rc, 1.0 + 0 * s.rc, 1.4), 0.1)
+    assert np.abs(Ur[1]).max() < 1e-14 and np.abs(Ur[0] - 1.0).max() < 1e-14
+    # the cylinder's rarefaction runs inward from r = 0.5 and the shock outward
+    r, (rho, u, p) = radial.circular_sod(0.2, n=1000)
+    assert rho[np.argmin(np.abs(r - 0.1))] == pytest.approx(1.0, abs=1e-12)
+    assert rho[np.argmin(np.abs(r - 1.5))] == pytest.approx(0.125, abs=1e-12)
+    assert u[(r > 0.3) & (r < 0.8)].min() > 0.0
