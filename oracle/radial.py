@@ -5,9 +5,9 @@ The paper compares its circular Sod profiles at t = 0.2 with "the exact result".
 cylindrically symmetric flow that result is the solution of the 1D Euler equations in the radius
 with the geometric source of the divergence in polar coordinates,
     d(r U)/dt + d(r F)/dr = (0, p, 0),   U = (rho, rho u, E),  F = (rho u, rho u^2 + p, u (E + p)),
-computed here at high resolution.  It is the standard textbook construction (e.g. Toro,
-"Riemann Solvers and Numerical Methods for Fluid Dynamics", Ch. 17 on geometric source terms),
-written as a finite-volume scheme on cells [r_{i-1/2}, r_{i+1/2}]:
+computed here at high resolution.  It is the standard reduction of a cylindrically symmetric
+flow to one space dimension with a geometric source term, written as a finite-volume scheme on
+cells [r_{i-1/2}, r_{i+1/2}]:
   * cell "volumes" V_i = (r_{i+1/2}^2 - r_{i-1/2}^2) / 2 and face "areas" A = r (per radian), so
     mass and energy are conserved exactly and a fluid at rest stays at rest (the pressure source
     p_i (A_{i+1/2} - A_{i-1/2}) balances the pressure flux);
