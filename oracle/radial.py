@@ -12,7 +12,7 @@ cells [r_{i-1/2}, r_{i+1/2}]:
     mass and energy are conserved exactly and a fluid at rest stays at rest (the pressure source
     p_i (A_{i+1/2} - A_{i-1/2}) balances the pressure flux);
   * piecewise-linear primitive variables with the minmod limiter (MUSCL);
-  * the HLLC approximate Riemann solver with Davis / Einfeldt wave-speed estimates;
+  * the HLLC approximate Riemann solver with Davis wave-speed estimates (min / max of u -+ c);
   * SSP-RK3 in time at a CFL number below one half;
   * the axis r = 0 a mirror (no flux through a face of zero area), the outer radius transmissive.
 alpha = 0 gives the planar (1D Cartesian) scheme on the same cells, for the pins against the
