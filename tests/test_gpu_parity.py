@@ -399,11 +399,14 @@ def test_positivity_fallback_kernel_parity(c1):
     assert max(err) < TOL_FP64, err
 
 
-@pytest.mark.parametrize("n", [7, 9])
+@pytest.mark.parametrize("n", [3, 4, 5, 7, 9])
 def test_tiny_periodic_mesh_kernel_parity(n):
-    """Degenerate size: a 7x7 / 9x9 torus (49 / 81 vertices, less than one thread block),
-    where the two-level sets and the 6-node stencils wrap around most of the mesh.  Smooth
-    random data; vertices whose sensor value lies within 1e-9 of a threshold are excluded."""
+    """Degenerate sizes: 3x3 to 9x9 tori (9 to 81 vertices, less than one thread block), where
+    the two-level sets cover most or all of the mesh and the 6-node stencils wrap around it
+    (below 7x7 a stencil spans more than half the period, so its minimum-image geometry is not
+    the physical one; both sides take the same reading, and the case checks the indexing).
+    Smooth random data; vertices whose sensor value lies within 1e-9 of a threshold are
+    excluded."""
     pkg = _hfd()
     m = synth.jittered_grid(n, n, 1.0, 1.0, seed=9)
     P = oracle.prepare(m)
