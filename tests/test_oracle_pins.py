@@ -806,3 +806,54 @@ def test_radial_reference_conserves_and_keeps_rest():
     assert rho[np.argmin(np.abs(r - 0.1))] == pytest.approx(1.0, abs=1e-12)
     assert rho[np.argmin(np.abs(r - 1.5))] == pytest.approx(0.125, abs=1e-12)
     assert u[(r > 0.3) & (r < 0.8)].min() > 0.0
+
+
+# ------------------------------------------------------------------ stencils and time step
+
+def test_stencils_of_grid_lines_are_the_straight_lines():
+    """Sec. 2.1: extension by the smallest deflection.  On an unjittered split grid every
+    horizontal or vertical edge has its straight continuation at both ends (deflection 0), so
+    its 6-node stencil is the row / column of grid points i-2 .. i+3, whatever the diagonals."""
+    n = 10
+    m = synth.jittered_grid(n, n, 10.0, 10.0, seed=3, jitter=0.0)
+    topo = oracle.build_topology(m)
+    checked = 0
+    for e, (a, b) in enumerate(topo["edges"]):
+        ia, ja, ib, jb = a % n, a // n, b % n, b // n
+        di, dj = (ib - ia + n // 2) % n - n // 2, (jb - ja + n // 2) % n - n // 2
+        if (abs(di), abs(dj)) not in ((1, 0), (0, 1)):
+            continue
+        ids, _ = oracle.edge_stencil(m, topo, e)
+        expect = [((ia + k * di) % n) + n * ((ja + k * dj) % n) for k in (-2, -1, 0, 1, 2, 3)]
+        assert list(ids) == expect, (e, ids, expect)
+        checked += 1
+    assert checked == 2 * n * n
+
+
+def test_two_level_vertex_sets_by_breadth_first_search():
+    """R7 against an independent construction: networkx's radius-2 ego graph of the mesh
+    graph, and every mesh edge with both ends in it."""
+    nx = pytest.importorskip("networkx")
+    m = synth.jittered_grid(9, 7, 9.0, 7.0, seed=5)
+    topo = oracle.build_topology(m)
+    G = nx.Graph()
+    G.add_edges_from(map(tuple, np.asarray(topo["edges"]).tolist()))
+    for v in range(len(m["x"])):
+        verts, edges = oracle.vertex_stencil(topo, v)
+        ref = sorted(nx.ego_graph(G, v, radius=2).nodes)
+        assert list(verts) == ref
+        sv = set(ref)
+        ref_e = sorted(k for k, (a, b) in enumerate(np.asarray(topo["edges"]).tolist())
+                       if a in sv and b in sv)
+        assert list(edges) == ref_e
+
+
+def test_cfl_step_closed_form():
+    """R12: dt = 0.3 min_v l_min(v) / (|u| + c); for a uniform flow on an unjittered grid of
+    spacing h, l_min = h at every vertex."""
+    m = synth.jittered_grid(8, 8, 4.0, 4.0, seed=1, jitter=0.0)
+    U = synth.uniform_state(m, rho=1.2, u=0.3, v=-0.4, p=0.9)
+    P = oracle.prepare(m)
+    c = np.sqrt(1.4 * 0.9 / 1.2)
+    assert oracle.cfl_dt(m, P, U) == pytest.approx(0.3 * 0.5 / (0.5 + c), rel=1e-14)
+
