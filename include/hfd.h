@@ -233,7 +233,8 @@ hfd_status hfd_steps_host(hfd_mesh* mesh, const double* U_in, double* U_out, dou
  * launch on `stream`; synchronises the stream and accumulates into kernel_ms[6] the time spent
  * in each kernel kind: [0] ghost refresh, [1] vertex fluxes, [2] edge interpolation + Riemann
  * flux, [3] divergence + RK stage, [4] time-step reduction, [5] persistent stage kernel.
- * Returns the launch count in *launches.  Tracing aid: events add a few microseconds each. */
+ * Returns in *launches the number of kernels launched (the time-step reduction is two).
+ * Tracing aid: events add a few microseconds each. */
 hfd_status hfd_steps_profiled(hfd_mesh* mesh, double* U, double dt, int32_t nsteps, void* stream,
                               double* kernel_ms, int64_t* launches);
 
