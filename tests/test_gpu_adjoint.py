@@ -41,7 +41,7 @@ def test_adjoint_step_matches_oracle_adjoint_20x20(conservative, flux):
     assert err < 1e-11, err
 
 
-@pytest.mark.parametrize("kind", ["transmissive", "walls"])
+@pytest.mark.parametrize("kind", ["transmissive", "walls", "delaunay"])
 def test_adjoint_step_with_ghost_layers_matches_oracle_adjoint(kind):
     """Meshes with ghost layers: transmissive ghosts on a box (5 layers), and the fixed wall
     bands of the channel (donor -1, 6 layers), each with a smooth inviscid state.  The GPU
@@ -52,9 +52,12 @@ def test_adjoint_step_with_ghost_layers_matches_oracle_adjoint(kind):
     if kind == "transmissive":
         m = synth.jittered_box_with_ghosts(16, 16, (0.0, 1.0), (0.0, 1.0), 5, seed=5)
         U = synth.isentropic_vortex(m, beta=2.0, center=(0.5, 0.5), mean=(1.0, 0.5))
-    else:
+    elif kind == "walls":
         m = synth.couette_channel(16, 17, 6, seed=7)
         U = synth.isentropic_vortex(m, beta=2.0, center=(0.0, 0.0), mean=(0.5, 0.0))
+    else:                                    # the embedded-circle Delaunay mesh, 5 ghost layers
+        m = synth.embedded_circle_box(16, seed=8)
+        U = synth.isentropic_vortex(m, beta=1.0, center=(0.0, 0.0), mean=(0.5, 0.3))
     P = oracle.prepare(m)
     dt = 0.5 * oracle.cfl_dt(m, P, U)
     lam = np.random.default_rng(1).standard_normal(U.shape)
@@ -71,7 +74,7 @@ def test_adjoint_step_with_ghost_layers_matches_oracle_adjoint(kind):
     err = np.linalg.norm(out - ref) / np.linalg.norm(ref)
     assert err < 1e-11, err
     g, dn = m["ghost_ids"], m["ghost_donor"]
-    if kind == "transmissive":
+    if kind != "walls":
         assert np.all(out[:, g] == 0.0)
     else:
         assert np.all(dn < 0) and np.linalg.norm(out[:, g]) > 0.0
