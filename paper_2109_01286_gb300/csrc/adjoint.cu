@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(128) k_adj_ghost_T(int nd, int V, const int32_
 
 }  // namespace hfd
 
-// ------------------------------------------------------------------ host driver
+// ------------------------------------------------------------------ host side
 using hfd::set_error;
 
 #define ACK(call)                                                                          \
