@@ -142,3 +142,39 @@ def test_adjoint_rollout_against_central_differences():
         fd = (jp - jm) / (2 * eps)
         ad = torch.sum(g * d).item()
         assert abs(fd - ad) <= 1e-5 * max(abs(fd), 1e-12), (fd, ad)
+
+
+def test_adjoint_rollout_with_ghost_layers_against_central_differences():
+    """The checkpointed rollout on a box with 5 transmissive ghost layers: <grad, delta>
+    against central differences of J = sum over physical vertices of A_v (rho - rho_ref)^2.
+    Perturbations of the ghost columns change nothing (every step refreshes them), and the
+    gradient there is zero."""
+    pkg = _pkg()
+    m = synth.jittered_box_with_ghosts(24, 24, (0.0, 1.0), (0.0, 1.0), 5, seed=12)
+    U0 = synth.isentropic_vortex(m, beta=2.0, center=(0.5, 0.5), mean=(1.0, 0.5))
+    mesh = pkg.Mesh(m)
+    dt = 0.002
+    perm = torch.from_numpy(mesh.perm.astype(np.int64)).cuda()
+    area = torch.from_numpy(synth.vertex_areas(m)).cuda()
+    area[torch.from_numpy(m["ghost_ids"].astype(np.int64)).cuda()] = 0.0
+    rho_ref = torch.from_numpy(synth.isentropic_vortex(m, beta=2.0, center=(0.5, 0.5),
+                                                       mean=(1.0, 0.5), t=6 * dt)[0]).cuda()
+    area_i, rho_ref_i = area[perm], rho_ref[perm]
+
+    def J(Ui):
+        UN = pkg.autograd.rollout(Ui, mesh, dt, 6, every=2)
+        return torch.sum(area_i * (UN[0] - rho_ref_i) ** 2)
+
+    U0i = mesh.import_state(torch.from_numpy(U0).cuda()).requires_grad_(True)
+    J(U0i).backward()
+    g = U0i.grad.detach()
+    ghosts_i = torch.isin(perm, torch.from_numpy(m["ghost_ids"].astype(np.int64)).cuda())
+    assert torch.all(g[:, ghosts_i] == 0.0)
+    rng = np.random.default_rng(8)
+    for _ in range(4):
+        d = mesh.import_state(torch.from_numpy(rng.standard_normal(U0.shape)).cuda())
+        eps = 1e-6
+        with torch.no_grad():
+            fd = (J((U0i + eps * d).detach()).item() - J((U0i - eps * d).detach()).item()) / (2 * eps)
+        ad = torch.sum(g * d).item()
+        assert abs(fd - ad) <= 1e-5 * max(abs(fd), 1e-12), (fd, ad)
