@@ -216,3 +216,26 @@ def test_invalid_meshes_are_rejected(pkg):
     with pytest.raises(pkg.HfdError) as e:
         pkg.Prep(tiny)
     assert e.value.status == 3
+
+
+def test_roofline_accounting_matches_the_per_vertex_stage_budget(pkg):
+    """bench.py's algorithmic bytes per launch (the numerator of the roofline fractions), summed
+    over the three kernels of a stage on a periodic mesh, per vertex: about 4.0 KB in FP64 and
+    2.3 KB in FP32 bulk (the budget of divergence coefficients, edge weights, indices, state,
+    fluxes and normals), and the divergence's share is the largest."""
+    import bench
+    m = synth.jittered_grid(40, 40, 10.0, 10.0, seed=1)
+    prep = pkg.Prep(m)
+    vptr, eptr = prep.get("div_vptr"), prep.get("div_eptr")
+    stats = {"nv": len(m["x"]), "nactive": len(prep.get("active")),
+             "nflux_edges": len(prep.get("flux_edges")),
+             "div_nv_total": int(vptr[-1]), "div_ne_total": int(eptr[-1])}
+    for T, lo, hi in ((8, 3500, 4600), (4, 1900, 2800)):
+        c = bench.algorithmic_costs(stats, T)
+        per_vertex = sum(c[k]["bytes"] for k in ("vertex", "edge", "div")) / stats["nv"]
+        assert lo < per_vertex < hi, (T, per_vertex)
+        assert c["div"]["bytes"] > c["edge"]["bytes"] > c["vertex"]["bytes"]
+        assert c["ghost"]["bytes"] == 0                       # periodic: no ghost vertices
+    # the flops: 48 per stencil vertex and 24 per stencil edge (12 rows x 2 or 1 multiply-adds)
+    c = bench.algorithmic_costs(stats, 8)
+    assert c["div"]["flops"] == 48 * vptr[-1] + 24 * eptr[-1] + 48 * stats["nactive"]
