@@ -14,7 +14,10 @@ of the same steps (hfd_steps_profiled); the roofline object describes the domina
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--n 1024]
 
 --impl reference times the FP64 CPU oracle (the reference arm of this comparison) on a bounded
-patch of the same workload on the host cores.
+patch of the same workload on one host core.  The default line's cpu_baseline reports the same
+oracle on one core and, under "all_cores", one oracle process per host core at once.
+
+Other workloads (--workload): batched, adjoint, tgv, conservative, circular-sod, vortex-order.
 """
 import argparse
 import json
