@@ -17,7 +17,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
-#include <mutex>
 
 #include "kernels.hpp"
 #include "mesh.hpp"
@@ -29,33 +28,19 @@ static __device__ __align__(256) unsigned char g_static_scratch[HFD_STATIC_SCRAT
 
 namespace {
 
-std::mutex g_static_mu;
-void* g_static_addr[256] = {};   // device address of g_static_scratch, per device ordinal
-
 // In host code g_static_scratch names a host-side stand-in, not device memory: the kernels
-// must be given the device address, looked up once per device with that device current.
+// must be given the device address, looked up with the mesh's device current.  The lookup is
+// repeated on every call (it allocates nothing and costs a host-side table search once the
+// library's device code is loaded): a cached address would go stale if the device's context
+// were destroyed and created again (cudaDeviceReset), since the array may then live elsewhere.
 hfd_status static_scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    hfd::set_error("hfd_residual_static: cudaGetDevice: %s", cudaGetErrorString(e));
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) {
+    hfd::set_error("hfd_residual_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     return HFD_ERR_CUDA;
   }
-  if (dev < 0 || dev >= 256) {
-    hfd::set_error("hfd_residual_static: device ordinal %d out of range", dev);
-    return HFD_ERR_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) {
-      hfd::set_error("hfd_residual_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-      return HFD_ERR_CUDA;
-    }
-    g_static_addr[dev] = p;
-  }
-  *out = g_static_addr[dev];
+  *out = p;
   return HFD_OK;
 }
 
