@@ -37,12 +37,23 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "vertex-stage updates/s"
-FP64_PEAK_FLOPS = 1.258e12       # GB300 FP64: 152 SMs x 2 DFMA/clk (ncu peak_sustained) x 2 x 2.07 GHz
 CPU_PATCH_N = 32                 # bounded oracle sample: 32 x 32 patch of the same workload
-# DRAM bytes (read + write) per launch on the default 1024 x 1024 workload, from one ncu capture
-# of the current kernels (profiles/traffic_four_quadrant_1024x1024.md); other sizes report null
-DRAM_TRAFFIC_1024 = {"k_div<double>": 3264.2e6, "k_edge<double>": 1090.3e6,
-                     "k_div<float>": 1755.4e6, "k_edge<float>": 580.6e6}
+# DRAM bytes (read + write) per launch of each kernel on the default 1024 x 1024 workload, from
+# one ncu capture per kernel (one launch, one-pass metrics; profiles/traffic_four_quadrant_1024x1024.md),
+# valid for the kernel and data-layout sources they were taken on: when either file's hash
+# differs the figures are stale and the line reports traffic as null
+TRAFFIC_SOURCES = ("paper_2109_01286_gb300/csrc/kernels.cu", "paper_2109_01286_gb300/csrc/api.cu")
+TRAFFIC_SHA = "71973a0b49482f39"
+DRAM_TRAFFIC_1024 = {"k_div<double>": 3286.9e6, "k_edge<double>": 1092.6e6,
+                     "k_div<float>": 1795.3e6, "k_edge<float>": 583.4e6}
+
+
+def sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -54,8 +65,12 @@ def parse():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp32-div", default="unstaged", choices=["unstaged", "staged"],
+                    help="divergence kernel of the FP32-bulk path (hfd_mesh_set_div_staged)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the bounded batched / adjoint / Taylor-Green passes of the default line")
     ap.add_argument("--workload", default="four-quadrant",
-                    choices=["four-quadrant", "batched", "adjoint", "tgv", "conservative",
+                    choices=["four-quadrant", "batched", "adjoint", "tgv", "conservative", "couette",
                              "circular-sod", "vortex-order"],
                     help="batched: 256 uneven isentropic-vortex meshes advanced together; "
                          "adjoint: gradient of a 200-step vortex run, checked by differences; "
@@ -147,6 +162,17 @@ def algorithmic_costs(stats, T):
                 + V * 8 * T + Ef * 4 * T, "flops": 48 * nv + 24 * ne + 48 * A},
         "ghost": {"bytes": (V - A) * (12 + 96 + 96), "flops": 0},
     }
+
+
+def fma_peaks():
+    """FP64 and FP32 FMA throughput of this device, measured by the library's hand-written FMA
+    loops (hfd_measure_fma_peaks) at the clocks it runs now, before any timed region."""
+    from paper_2109_01286_gb300 import measure_fma_peaks
+    m = measure_fma_peaks()
+    return {"fp64_tflops": m["fp64_flops"] / 1e12, "fp32_tflops": m["fp32_flops"] / 1e12,
+            "sm_count": m["sm_count"],
+            "source": f"measured: hand-written FP64 FMA loop on all {m['sm_count']} SMs "
+                      "(hfd_measure_fma_peaks), best of 3 launches"}
 
 
 def load_peaks():
@@ -267,8 +293,11 @@ def run_native(args):
     results = {}
     clocks_main = None
     peak_hbm, peak_src = load_peaks()
+    fpk = fma_peaks()
     for prec in ("fp64", "fp32"):
         dm = prep.upload(prec)
+        if prec == "fp32" and args.fp32_div == "staged":
+            dm.set_div_staged(1)
         st = dm.stats_dict()
         Ui = dm.import_state(U_dev)
         # Every timed step advances the initial state of the workload: the method as read here
@@ -329,6 +358,31 @@ def run_native(args):
         X.copy_(Ui)
         dm.step(X, 0.0)
         results[prec]["one_step"] = dm.export_state(X)[0:4].cpu().numpy()
+        # the same steps timed from a developed state: the state after two steps (the method's
+        # growth makes later states of this problem inadmissible), with the branch mix of both
+        if not args.no_variants:
+            D = Ui.clone()
+            dm.steps(D, 0.0, 2)
+            torch.cuda.synchronize()
+            finite2 = bool(torch.isfinite(D).all())
+            weno = {"initial": int(np.unpackbits(dm.edge_branches(Ui)).sum()),
+                    "after_2_steps": int(np.unpackbits(dm.edge_branches(D)).sum())}
+            for _ in range(args.warmup):
+                X.copy_(D)
+                dm.steps(X, 0.0, 1)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                X.copy_(D)
+                dm.steps(X, 0.0, 1)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            dv, _, dms = replicas.whole_job_rate(A * 3 * args.steps, ev0.elapsed_time(ev1), dist,
+                                                 device="cuda")
+            results[prec]["developed"] = {
+                "value": dv, "ms_per_step": dms / args.steps, "state_finite": finite2,
+                "weno_sides_and_components": weno,
+                "step_input": "every timed step advances the state after two steps"}
         if prec == "fp64":
             e2e = None
             if not args.no_e2e:
@@ -359,19 +413,20 @@ def run_native(args):
     r = results["fp64"]
     dom = max(r["kernels"], key=lambda k: r["kernels"][k]["share"])
     kd = r["kernels"][dom]
+    fresh = TRAFFIC_SHA is not None and sources_sha() == TRAFFIC_SHA
+
     def traffic(name):
-        return DRAM_TRAFFIC_1024.get(name) if args.n == 1024 else None
+        return DRAM_TRAFFIC_1024.get(name) if (args.n == 1024 and fresh) else None
 
     def dram(name, avg_ms):
         # the survey's % of HBM: measured DRAM bytes per launch over the live launch time
         t = traffic(name)
         return (None, None) if t is None else (t / (avg_ms / 1000.0) / 1e9, t / (avg_ms / 1000.0) / 1e9 / peak_hbm)
     roof = {"kernel": f"k_{dom}<double>", "bound": "alu", "achieved": kd["tflops"],
-            "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-            "frac": kd["tflops"] / (FP64_PEAK_FLOPS / 1e12), "traffic": traffic(f"k_{dom}<double>"),
+            "peak": fpk["fp64_tflops"], "unit": "TFLOP/s",
+            "frac": kd["tflops"] / fpk["fp64_tflops"], "traffic": traffic(f"k_{dom}<double>"),
             "traffic_unit": "bytes per launch (ncu DRAM read + write)",
-            "peak_source": "derived: ncu dfma peak_sustained 2/SM/clk x 152 SMs x 2 flop x 2.07 GHz "
-                           "(MEASURED_PEAKS.json has no FP64 figure)",
+            "peak_source": fpk["source"],
             "hbm_gbs": kd["gbs"], "hbm_frac": kd["gbs"] / peak_hbm,
             "dram_gbs": dram(f"k_{dom}<double>", kd["avg_ms"])[0],
             "dram_frac": dram(f"k_{dom}<double>", kd["avg_ms"])[1],
@@ -408,6 +463,8 @@ def run_native(args):
                          "peak_source": peak_src},
             "kernels": f32["kernels"]}},
         "state_finite": r["finite"],
+        "developed_state": {"fp64": r.get("developed"), "fp32_bulk": f32.get("developed")},
+        "fma_peaks": fpk,
         "gpu_launches": int(r["launches"]),
         "e2e": r.get("e2e"),
         "clocks": clocks_main,
@@ -436,31 +493,137 @@ def run_native(args):
                           f"{steps} steps in all, over the union of their timed windows"}
         except Exception as e:                        # the single-core figure stands alone
             line["cpu_baseline"]["all_cores"] = {"unavailable": str(e)[:200]}
+    if not args.no_variants:
+        # bounded passes of the batched, adjoint and viscous configurations (after the timed
+        # regions of the line's own workload)
+        for key, fn in (("batched_subset", lambda: variant_batched(fpk, steps=min(args.steps, 10))),
+                        ("adjoint_cost", variant_adjoint), ("tgv_mixed_precision", variant_tgv)):
+            try:
+                line["variants"][key] = fn()
+            except Exception as e:                    # reported, never fatal to the line
+                line["variants"][key] = {"error": str(e)[:300]}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-# ------------------------------------------------------------------ batched workload
-def run_batched(args):
-    """Many uneven meshes advanced together (one union mesh, autotuned launch shape, graph of RK
-    stages) against looping the same meshes one at a time (one graph per mesh).  Under torchrun
-    the meshes are partitioned over the ranks (no data-path collective); the whole-job rate is
-    all ranks' vertex-stage updates over the slowest rank's time."""
-    import torch
-    from paper_2109_01286_gb300 import Prep, replicas
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    every = synth.batched_vortices(n=args.batch, seed=4)
-    members = [every[i] for i in replicas.shard(len(every), rank, world)]
+# ------------------------------------------------------------------ short variants of the other configs
+def variant_batched(fpk, members_n=32, steps=10, warmup=3):
+    """A bounded pass of the batched configuration in the default line: the first `members_n`
+    of the 256 uneven isentropic-vortex meshes (host preprocessing of all 256 takes minutes;
+    --workload batched runs them all)."""
+    from paper_2109_01286_gb300 import Prep
+    every = synth.batched_vortices(n=256, seed=4)
+    members = every[:members_n]
     t0 = time.perf_counter()
     preps = [Prep(x["mesh"]) for x in members]
     prep_s = time.perf_counter() - t0
+    out = batched_pass(members, preps, steps, warmup, fpk)
+    keys = ("value", "ms_per_step", "speedup_vs_looped", "looped_singles_value", "launch", "roofline")
+    return {"workload": f"first {members_n} of the 256 batched isentropic vortices "
+                        "(log-uniform 2e3-6.4e4 vertices, aspect 1-4), each its own CFL step",
+            "physical_vertices": int(sum(x["U"].shape[1] for x in members)), "steps": steps,
+            "prep_seconds": prep_s,
+            "fp64": {k: out["fp64"][k] for k in keys},
+            "fp32_bulk": {k: out["fp32"][k] for k in keys}}
+
+
+def variant_adjoint(reps=10, horizon=20, every=4):
+    """Cost of the discrete adjoint on the adjoint configuration's mesh (256 x 256 periodic
+    vortex, FP64, device CFL step of the initial state): one hfd_adjoint against one hfd_step,
+    and a checkpointed rollout's backward pass against its forward pass."""
+    import torch
+    from paper_2109_01286_gb300 import Mesh
+    from paper_2109_01286_gb300.autograd import rollout
+    m = synth.jittered_grid(256, 256, 10.0, 10.0, seed=5)
+    mesh = Mesh(m)
+    U0 = mesh.import_state(torch.from_numpy(synth.isentropic_vortex(m, beta=5.0)).cuda())
+    probe = U0.clone()
+    mesh.step(probe, 0.0)
+    dt = float(mesh.last_dt())
+    stream = torch.cuda.current_stream()
+    lam = torch.ones_like(U0)
+    X = U0.clone()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    step_ms = timed(lambda: mesh.step(X.copy_(U0), dt))
+    adj_ms = timed(lambda: mesh.adjoint(U0, lam, dt=dt))
+    Ui = U0.clone().requires_grad_(True)
+    t_fwd = timed(lambda: rollout(Ui, mesh, dt, horizon, every))
+
+    def fwd_bwd():
+        Ui.grad = None
+        rollout(Ui, mesh, dt, horizon, every)[0].sum().backward()
+    t_both = timed(fwd_bwd)
+    mesh.check()
+    return {"workload": "256x256 periodic isentropic vortex, FP64, fixed step (device CFL 0.3 of "
+                        "the initial state)",
+            "step_ms": step_ms, "adjoint_ms": adj_ms, "adjoint_over_step": adj_ms / step_ms,
+            "rollout": {"steps": horizon, "checkpoint_every": every, "forward_ms": t_fwd,
+                        "backward_ms": t_both - t_fwd,
+                        "backward_over_forward": (t_both - t_fwd) / t_fwd}}
+
+
+def variant_tgv(steps=(1, 5, 20)):
+    """Mixed-precision accuracy on the viscous Taylor-Green configuration (512 x 512, Re 100,
+    Mach 0.1, Pr 0.72): FP32 bulk against FP64 after a few steps, and each path's velocity
+    against the incompressible decay exp(-2 nu t)."""
+    import torch
+    from paper_2109_01286_gb300 import Prep
+    n, mach, re = 512, 0.1, 100.0
+    p0 = 1.0 / (1.4 * mach * mach)
+    m = synth.jittered_grid(n, n, 2 * np.pi, 2 * np.pi, seed=3)
+    U0 = synth.taylor_green(m, mach=mach)
+    prep = Prep(m, viscous=True, mu=1.0 / re, R_gas=p0, prandtl=0.72)
+    dt = 0.3 * (2 * np.pi / n) / (1.0 + np.sqrt(1.4 * p0))
+    got = {}
+    for prec in ("fp64", "fp32"):
+        mesh = prep.upload(prec)
+        X = mesh.import_state(torch.from_numpy(U0).cuda())
+        done, got[prec] = 0, {}
+        for k in steps:
+            mesh.steps(X, dt, k - done)
+            done = k
+            got[prec][k] = mesh.export_state(X).cpu().numpy()
+        del mesh
+    decay = lambda t: np.exp(-2.0 * t / re)
+
+    def vel_err(U, t):
+        uex = np.sin(m["x"]) * np.cos(m["y"]) * decay(t)
+        vex = -np.cos(m["x"]) * np.sin(m["y"]) * decay(t)
+        u, v = U[1] / U[0], U[2] / U[0]
+        return float(np.sqrt(np.mean((u - uex) ** 2 + (v - vex) ** 2) / np.mean(uex ** 2 + vex ** 2)))
+    rows = []
+    for k in steps:
+        a, b = got["fp64"][k], got["fp32"][k]
+        rows.append({"step": k,
+                     "fp32_vs_fp64_rel_l2_all_rows": float(np.linalg.norm(a - b) / np.linalg.norm(a)),
+                     "fp32_vs_fp64_rel_l2_w": float(np.linalg.norm(a[:4] - b[:4]) / np.linalg.norm(a[:4])),
+                     "velocity_vs_decay_fp64": vel_err(a, k * dt),
+                     "velocity_vs_decay_fp32": vel_err(b, k * dt)})
+    return {"workload": f"viscous Taylor-Green {n}x{n}, Re {re:g}, Mach {mach}, Pr 0.72, steps of "
+                        f"{dt:.4g}", "checkpoints": rows}
+
+
+# ------------------------------------------------------------------ batched workload
+def batched_pass(members, preps, steps, warmup, fpk, dist=None):
+    """The batch of `members` (with their preps) advanced as one device mesh (autotuned launch
+    shape, CUDA graph of RK steps, every member its own CFL step) for `steps` timed steps, and
+    the same meshes looped one at a time; FP64 and FP32 bulk.  Returns per precision the rates,
+    the speed-up over the loop, the launch choice, the per-kernel times and the roofline of the
+    dominant kernel."""
+    import torch
+    from paper_2109_01286_gb300 import Prep, replicas
+    args = argparse.Namespace(steps=steps, warmup=warmup)
     Ub = np.concatenate([x["U"] for x in members], axis=1)
     stream = torch.cuda.current_stream()
     out = {}
@@ -493,8 +656,8 @@ def run_batched(args):
         peak_hbm, peak_src = load_peaks()
         if prec == "fp64":
             roof = {"kernel": f"k_{dom}<double>", "bound": "alu",
-                    "achieved": costs[dom]["flops"] / avg_s / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
-                    "unit": "TFLOP/s", "traffic": None,
+                    "achieved": costs[dom]["flops"] / avg_s / 1e12, "peak": fpk["fp64_tflops"],
+                    "unit": "TFLOP/s", "traffic": None, "peak_source": fpk["source"],
                     "hbm_gbs": costs[dom]["bytes"] / avg_s / 1e9}
             roof["frac"] = roof["achieved"] / roof["peak"]
         else:
@@ -523,8 +686,32 @@ def run_batched(args):
                      "looped_singles_value": loop_value,
                      "looped_singles_ms_per_step": ms_loop / args.steps,
                      "speedup_vs_looped": ms_loop / ms,
-                     "launch": {"persistent": choice[0], "grid": choice[1], "lanes": choice[2]},
+                     "launch": {"persistent": choice[0], "grid": choice[1], "lanes": choice[2], "staged_div": choice[3]},
                      "kernels_ms": kms, "launches": nl, "roofline": roof}
+    return out
+
+
+def run_batched(args):
+    """Many uneven meshes advanced together (one union mesh, autotuned launch shape, graph of RK
+    stages) against looping the same meshes one at a time (one graph per mesh).  Under torchrun
+    the meshes are partitioned over the ranks (no data-path collective); the whole-job rate is
+    all ranks' vertex-stage updates over the slowest rank's time."""
+    import torch
+    from paper_2109_01286_gb300 import Prep, replicas
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    every = synth.batched_vortices(n=args.batch, seed=4)
+    members = [every[i] for i in replicas.shard(len(every), rank, world)]
+    t0 = time.perf_counter()
+    preps = [Prep(x["mesh"]) for x in members]
+    prep_s = time.perf_counter() - t0
+    fpk = fma_peaks()
+    out = batched_pass(members, preps, args.steps, args.warmup, fpk, dist)
     if dist is not None:
         dist.destroy_process_group()
     if rank != 0:
@@ -817,6 +1004,62 @@ def run_vortex_order(args):
 
 
 # ------------------------------------------------------------------ circular Sod workload
+def run_couette(args):
+    """Compressible Couette flow of Sec. 3.2 marched in time: walls at y = -5 and +5 moving at
+    -u0 and +u0 held by 6 fixed ghost layers each (the exact solution), x periodic on [-5, 5),
+    gamma 1.4, c_p 10, conductivity 1/100, viscosity 1/10 (the paper's constants; the wall
+    speed and temperatures it leaves out are u0 = 1, T = 10 and 12, p = 10).  Jittered
+    random-split meshes with the paper's 35, 70, 105 and 140 segments per side, FP64, started
+    from the exact steady solution with a fixed step proportional to h (CFL 0.3 of the finest
+    mesh scaled by h): the area-weighted L2 density error against the exact solution at
+    checkpoints, and the order between consecutive meshes, while the states stay finite."""
+    import torch
+    from paper_2109_01286_gb300 import Mesh
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    Ns, marks = (35, 70, 105, 140), (0.05, 0.1, 0.2, 0.5, 1.0, 2.0)
+    visc = dict(viscous=True, mu=0.1, prandtl=100.0, R_gas=0.4 * 10.0 / 1.4)
+    quantum = 0.05
+    errs, meshes = {}, []
+    for N in Ns:
+        m = synth.couette_channel(N, N + 1, 6, seed=7)
+        U0 = synth.couette(m)
+        mesh = Mesh(m, **visc)
+        phys = np.ones(len(m["x"]), bool)
+        phys[m["ghost_ids"]] = False
+        A = synth.vertex_areas(m)[phys]
+        X = mesh.import_state(torch.from_numpy(U0).cuda())
+        probe = X.clone()
+        mesh.step(probe, 0.0)
+        dt_cfl = float(mesh.last_dt())
+        k = int(np.ceil(quantum / dt_cfl))          # steps per quantum: checkpoints on steps
+        dt = quantum / k
+        done, errs[N] = 0.0, {}
+        for t in marks:
+            nsteps = int(round((t - done) / dt))
+            mesh.steps(X, dt, nsteps)
+            done = t
+            U = mesh.export_state(X).cpu().numpy()
+            if not np.all(np.isfinite(U[:, phys])):
+                break
+            errs[N][t] = float(np.sqrt(np.sum(A * (U[0, phys] - U0[0, phys]) ** 2) / A.sum()))
+        meshes.append({"segments": N, "vertices": len(m["x"]), "physical": int(phys.sum()),
+                       "dt": dt, "finite_until": max(errs[N]) if errs[N] else 0.0})
+        del mesh
+    table = []
+    for t in marks:
+        row = {"t": t, "rho_l2": [errs[N].get(t) for N in Ns]}
+        e = row["rho_l2"]
+        row["orders"] = [float(np.log(e[i] / e[i + 1]) / np.log(Ns[i + 1] / Ns[i]))
+                         if e[i] and e[i + 1] else None for i in range(len(Ns) - 1)]
+        table.append(row)
+    line = {"metric": "density error vs exact", "workload": "couette", "data": "synthetic",
+            "config": {"workload": "compressible Couette flow (Sec. 3.2), walls at y = +-5 "
+                                   "with 6 fixed ghost layers, x periodic, 35/70/105/140 "
+                                   "segments per side, FP64, from the exact solution"},
+            "meshes": meshes, "checkpoints": table}
+    print(json.dumps(line), flush=True)
+
+
 def run_circular_sod(args):
     """Circular Sod problem (Sec. 3.3) on embedded-circle Delaunay meshes of [-1, 1]^2 whose
     sides are split into 50, 100 and 150 segments: FP64 SSP-RK3 steps at CFL 0.3 (device time
@@ -881,7 +1124,7 @@ def run_circular_sod(args):
                                "[-1,1]^2 with 50/100/150 segments per side, 5 ghost layers, "
                                "CFL 0.3; rate on the 150-segment mesh over "
                                f"{K} steps per pass from the initial state, autotuned launch"},
-        "launch": {"persistent": choice[0], "grid": choice[1], "lanes": choice[2]},
+        "launch": {"persistent": choice[0], "grid": choice[1], "lanes": choice[2], "staged_div": choice[3]},
         "ms_per_step_default_launch": ms_default,
         "runs": runs,
     }
@@ -898,6 +1141,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "tgv":
         run_tgv(args)
+    elif args.workload == "couette":
+        run_couette(args)
     elif args.workload == "circular-sod":
         run_circular_sod(args)
     elif args.workload == "vortex-order":

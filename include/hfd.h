@@ -247,12 +247,25 @@ hfd_status hfd_steps_profiled(hfd_mesh* mesh, double* U, double dt, int32_t nste
  * fixed 8 MiB array compiled into the library, held on every GPU that loads the library until
  * the process exits.  That is room for about 32,000 vertices in FP64 (256 bytes each with their
  * ~3 flux edges) or 65,000 in FP32 bulk; larger meshes get HFD_ERR_ARG with the bytes needed.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current), so make that first call before any stream capture.  All calls on a
+ * Every call looks up the array's device address (cudaGetSymbolAddress, with the mesh's device
+ * current), so the address stays right across a cudaDeviceReset; the first call on a device
+ * may also load the library's device code there, so make that first call before any stream
+ * capture.  All calls on a
  * device share the array: calls that overlap on the GPU race and must be serialised by the
  * caller.  Every call rewrites what it reads, so nothing carries over between calls.  Errors:
  * HFD_ERR_ARG (sizes, null pointers, mesh not on the current device), HFD_ERR_CUDA. */
 hfd_status hfd_residual_static(hfd_mesh* mesh, double* U, double* R, void* stream);
+
+/* Measured fused multiply-add throughput of the current device, for the arithmetic roofline of
+ * the FP64 path.  The paper has no counterpart: this is a measurement aid.  Hand-written loops
+ * of independent FMA chains (no memory traffic) run on every SM for about 25 ms per launch, in
+ * FP64 and then FP32; the best of three timed launches (after one warm-up) is returned as
+ * FLOP/s (2 per FMA) in *fp64_flops and *fp32_flops, and the device's SM count
+ * (cudaDevAttrMultiProcessorCount) in *sm_count.  The figures are at the clocks the device
+ * runs during the call.  Allocates and frees a small device buffer; synchronises the stream.
+ * Errors: HFD_ERR_ARG (null output), HFD_ERR_CUDA. */
+hfd_status hfd_measure_fma_peaks(double* fp64_flops, double* fp32_flops, int32_t* sm_count,
+                                 void* stream);
 
 /* Discrete adjoint of one step (gradients through the time stepping): given
  * lam_np1 = dJ/dU_{n+1}, writes lam_n = (d hfd_step(U_n, dt) / d U_n)^T lam_np1, the exact
@@ -295,13 +308,36 @@ hfd_status hfd_mesh_set_barrier_limit(hfd_mesh* mesh, uint32_t polls);
  * hfd_mesh_set_launch that the new count's kernel cannot hold co-resident). */
 hfd_status hfd_mesh_set_lanes(hfd_mesh* mesh, int32_t lanes);
 
+/* Testing aid: the branch of Alg. 1 (Eq. (2d_hweno_intp)) that the edge kernel takes on state U
+ * (12*nv device array, internal order; its ghost columns are refreshed): runs the ghost refresh,
+ * vertex fluxes and edge kernel once and writes, for every flux edge in the preprocessing's
+ * flux-edge order ("flux_edges" of hfd_prep_get), one byte to the HOST array branches[nflux_edges]
+ * (caller owned): bit side*4+q is set where characteristic component q of side L (0) or R (1)
+ * took the WENO-weighted 3-node value instead of the 5-node one.  The decision is the path's
+ * own (FP32 sensor with FP64 re-decision inside a guard band on FP64 meshes).  Allocates a
+ * temporary device block; synchronises the stream.  Errors: HFD_ERR_ARG, HFD_ERR_CUDA. */
+hfd_status hfd_edge_branches(hfd_mesh* mesh, double* U, uint8_t* branches, void* stream);
+
+/* Divergence kernel of an FP32-bulk mesh (the default is 0).  staged = 1: the staged kernel --
+ * a persistent, warp-specialised grid walks tiles of consecutive vertices whose row pointers,
+ * index chunks and coefficient chunks (the contiguous streams of the least-squares rows, Eq.
+ * (flux_polynomials)) one producer thread copies into shared memory with 1D bulk copies, up to
+ * three tiles ahead of eight consumer warps; 8 lanes per vertex.  staged = 0: the unstaged
+ * kernel with the lane count of hfd_mesh_set_lanes, which holds more vertices' gathers in
+ * flight per SM and measured faster on the four-quadrant 1024x1024 mesh (0.395 ms against
+ * 0.560 ms per launch on a GB300); the autotuner times both.  The two agree to rounding (bit
+ * for bit at 8 lanes).  Drops captured graphs.  Errors: HFD_ERR_ARG (staged not 0 or 1),
+ * HFD_ERR_UNSUPPORTED (staged = 1 on an FP64 mesh). */
+hfd_status hfd_mesh_set_div_staged(hfd_mesh* mesh, int32_t staged);
+
 /* Autotuner: times one Runge-Kutta stage on (a copy of) the device state U, internal order,
- * for every lane count of hfd_mesh_set_lanes in the four-launch form and for 1, 2 and 4 lanes
- * in the persistent form at every co-resident block count; keeps the fastest, and writes it to
- * choice[0] (persistent), choice[1] (grid) and choice[2] (lanes) if choice (3 int32, caller
- * owned) is not NULL.  The choice changes the launch shape and the divergence's summation
- * order, not the method's arithmetic (results agree to rounding, see hfd_mesh_set_launch and
- * hfd_mesh_set_lanes).  Synchronises. */
+ * for every lane count of hfd_mesh_set_lanes in the four-launch form (unstaged divergence),
+ * for the staged divergence of an FP32-bulk mesh (hfd_mesh_set_div_staged), and for 1, 2 and 4
+ * lanes in the persistent form at every co-resident block count; keeps the fastest, and writes
+ * it to choice[0] (persistent), choice[1] (grid), choice[2] (lanes) and choice[3] (staged) if
+ * choice (4 int32, caller owned) is not NULL.  The choice changes the launch shape and the
+ * divergence's summation order, not the method's arithmetic (results agree to rounding, see
+ * hfd_mesh_set_launch and hfd_mesh_set_lanes).  Synchronises. */
 hfd_status hfd_mesh_autotune(hfd_mesh* mesh, const double* U, void* stream, int32_t* choice);
 
 /* dt used by the most recent step, one value per member mesh (synchronises the stream). */

@@ -5,7 +5,7 @@ in-tree library `_lib/libhfd.so` (host C++ preprocessing + CUDA kernels for sm_1
 `build.build()`.
 """
 from . import hfd
-from .hfd import Batch, HfdError, Mesh, Prep, options
+from .hfd import Batch, HfdError, Mesh, Prep, measure_fma_peaks, options
 from . import autograd
 
-__all__ = ["hfd", "autograd", "Batch", "HfdError", "Mesh", "Prep", "options"]
+__all__ = ["hfd", "autograd", "Batch", "HfdError", "Mesh", "Prep", "measure_fma_peaks", "options"]

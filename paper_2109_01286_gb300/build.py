@@ -30,7 +30,7 @@ def _nvcc():
 
 def _sources():
     return [os.path.join(CSRC, f) for f in ("prep.cpp", "kernels.cu", "api.cu", "noalloc.cu",
-                                            "adjoint.cu")]
+                                            "adjoint.cu", "peaks.cu")]
 
 
 def _deps():

@@ -173,6 +173,50 @@ hfd_status upload_streams(hfd_mesh* m, const hfd::Prep& P, const std::vector<int
     // FP32 bulk: entries in chunks of 4 (hfd::kDivChunk), each chunk's rows contiguous
     chunk_rows(A, vptr, vidx, 6, cv, P.opts.viscous ? &cvis : nullptr);
     chunk_rows(A, eptr, eidx, 3, ce, static_cast<std::vector<T>*>(nullptr));
+    // tiles of the staged divergence: runs of at most kStageTileVerts consecutive vertices
+    // whose row pointers, index chunks and coefficient chunks fit one stage buffer; per tile
+    // {r0, r1, c0, nvc, m0, nec, pb, 0} with pb = r0 rounded down to a multiple of 4 (the
+    // 16-byte aligned start of the row-pointer copies)
+    std::vector<int32_t> tiles;
+    const size_t per_vc = 16 + 96 + (P.opts.viscous ? 96 : 0), per_ec = 16 + 48;
+    for (int r0 = 0; r0 < A;) {
+      int r1 = r0;
+      while (r1 < A && r1 - r0 < hfd::kStageTileVerts &&
+             2 * (size_t)hfd::kStagePtrSlot + per_vc * (size_t)(vptr[r1 + 1] - vptr[r0]) +
+                     per_ec * (size_t)(eptr[r1 + 1] - eptr[r0]) <=
+                 (size_t)hfd::kStageTileBytes)
+        ++r1;
+      if (r1 == r0) {
+        set_error("vertex %d has more divergence entries than one stage buffer holds", r0);
+        return HFD_ERR_MESH;
+      }
+      const int32_t rec[8] = {r0, r1, vptr[r0], vptr[r1] - vptr[r0], eptr[r0], eptr[r1] - eptr[r0],
+                              r0 & ~3, 0};
+      tiles.insert(tiles.end(), rec, rec + 8);
+      r0 = r1;
+    }
+    d.ntiles = (int)tiles.size() / 8;
+    d.div_staged = 0;                 // the unstaged kernel measured faster (see hfd.h)
+    TRY(dev_upload(m, (void**)&d.tiles, tiles));
+    // the row-pointer copies read whole int4s up to 3 entries past vptr[A] / eptr[A]
+    vptr.resize((size_t)A + 5, vptr[A]);
+    eptr.resize((size_t)A + 5, eptr[A]);
+    // every range the staged kernel reads, checked here once: copy extents inside the arrays,
+    // the row-pointer slots and the tile inside one stage buffer
+    for (int t = 0; t < d.ntiles; ++t) {
+      const int32_t* rc = &tiles[(size_t)8 * t];
+      const int r0 = rc[0], r1 = rc[1], pb = rc[6];
+      const int nseg = (r1 + 1 - pb + 3) & ~3;
+      const size_t bytes = 2 * (size_t)hfd::kStagePtrSlot + per_vc * rc[3] + per_ec * rc[5];
+      const bool ok = r0 < r1 && r1 - r0 <= hfd::kStageTileVerts && pb % 4 == 0 && pb <= r0 &&
+                      4 * nseg <= hfd::kStagePtrSlot && (size_t)(pb + nseg) <= vptr.size() &&
+                      (size_t)rc[2] + rc[3] <= (size_t)vptr[A] && (size_t)rc[4] + rc[5] <= (size_t)eptr[A] &&
+                      bytes <= (size_t)hfd::kStageTileBytes && (t == 0 || tiles[(size_t)8 * t - 7] == r0);
+      if (!ok) {
+        set_error("staged divergence tile %d fails its bounds (vertices %d..%d)", t, r0, r1);
+        return HFD_ERR_MESH;
+      }
+    }
   }
   TRY(dev_upload(m, (void**)&d.vptr, vptr));
   TRY(dev_upload(m, (void**)&d.eptr, eptr));
@@ -257,6 +301,7 @@ hfd_status upload(const hfd::Prep& P, int precision, hfd_mesh* m) {
     fint[fperm[i]] = i;
     emap[P.flux_edges[fperm[i]]] = i;
   }
+  m->fperm = fperm;
   hfd_status st = d.precision == 0 ? upload_streams<double>(m, P, inv, fint, fperm, emap)
                                    : upload_streams<float>(m, P, inv, fint, fperm, emap);
   if (st != HFD_OK) return st;
@@ -609,6 +654,49 @@ hfd_status hfd_mesh_set_lanes(hfd_mesh* m, int32_t lanes) {
   return HFD_OK;
 }
 
+hfd_status hfd_mesh_set_div_staged(hfd_mesh* m, int32_t staged) {
+  if (!m || (staged != 0 && staged != 1)) {
+    set_error("hfd_mesh_set_div_staged: staged must be 0 or 1");
+    return HFD_ERR_ARG;
+  }
+  if (staged && m->dm.ntiles == 0 && m->dm.A > 0) {
+    set_error("hfd_mesh_set_div_staged: the staged divergence exists for FP32-bulk meshes only");
+    return HFD_ERR_UNSUPPORTED;
+  }
+  m->dm.div_staged = staged;
+  drop_graphs(m);
+  return HFD_OK;
+}
+
+hfd_status hfd_edge_branches(hfd_mesh* m, double* U, uint8_t* branches, void* stream) {
+  if (!m || !U || !branches) {
+    set_error("hfd_edge_branches: invalid argument");
+    return HFD_ERR_ARG;
+  }
+  hfd::NvtxRange range("hfd_edge_branches");
+  DevMesh d = m->dm;
+  const int Ef = d.Ef;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<uint8_t> host((size_t)Ef);
+  if (Ef > 0) {
+    CK(mesh_malloc(m, (void**)&d.dbg_branch, (size_t)Ef));
+    cudaError_t e = hfd::launch_ghost(d, U, U, s);
+    if (e == cudaSuccess) e = hfd::launch_vertex(d, U, m->ph, s);
+    if (e == cudaSuccess) e = hfd::launch_edge(d, m->ph, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), d.dbg_branch, (size_t)Ef, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // the block is one of the mesh's (released with it); drop it from the list now
+    if (m->opts.dev_alloc) m->opts.dev_free(d.dbg_branch, m->opts.alloc_ctx); else cudaFree(d.dbg_branch);
+    m->allocs.pop_back();
+    if (e != cudaSuccess) {
+      set_error("hfd_edge_branches: %s", cudaGetErrorString(e));
+      return HFD_ERR_CUDA;
+    }
+  }
+  for (int fi = 0; fi < Ef; ++fi) branches[m->fperm[fi]] = host[fi];
+  return HFD_OK;
+}
+
 hfd_status hfd_mesh_set_barrier_limit(hfd_mesh* m, uint32_t polls) {
   if (!m) { set_error("hfd_mesh_set_barrier_limit: null mesh"); return HFD_ERR_ARG; }
   m->dm.barrier_spins = polls;
@@ -625,20 +713,22 @@ hfd_status hfd_mesh_autotune(hfd_mesh* m, const double* U, void* stream, int32_t
   CK(cudaMemcpyAsync(m->U1, U, bytes, cudaMemcpyDeviceToDevice, s));
   // candidates: lanes per vertex in the divergence x (four-launch form, persistent form at
   // every co-resident block count for those lanes)
-  struct Cand { int persistent, grid, lanes; };
+  struct Cand { int persistent, grid, lanes, staged; };
   std::vector<Cand> cands;
+  if (d.ntiles > 0) cands.push_back({0, 0, 8, 1});    // FP32 bulk: the staged divergence
   for (int lanes : {1, 2, 4, 8}) {
     int per_sm = 0, nsm = 0;
     CK(hfd::persistent_max_blocks(d, lanes, &per_sm, &nsm));
-    cands.push_back({0, 0, lanes});
+    cands.push_back({0, 0, lanes, 0});
     if (lanes == 8) continue;                  // the persistent kernel runs 8 lanes as 4
-    for (int b = 1; b <= per_sm; ++b) cands.push_back({1, b * nsm, lanes});
+    for (int b = 1; b <= per_sm; ++b) cands.push_back({1, b * nsm, lanes, 0});
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   Cand pick = cands[0];
+  DevMesh dd = d;                              // the trial's divergence kernel choice
   const double dt = 1e-12;   // any fixed step: the work does not depend on it
   for (const Cand& c : cands) {
     float tot = 0;
@@ -649,10 +739,11 @@ hfd_status hfd_mesh_autotune(hfd_mesh* m, const double* U, void* stream, int32_t
         CK(hfd::launch_stage_persistent(d, m->U1, m->U1, m->U2, hfd::DIV_STAGE, 0.0, 1.0, dt,
                                         m->ph, c.lanes, c.grid, true, s));
       } else {
+        dd.div_staged = c.staged;
         if (d.G) CK(hfd::launch_ghost(d, m->U1, m->U1, s));
         CK(hfd::launch_vertex(d, m->U1, m->ph, s));
         CK(hfd::launch_edge(d, m->ph, s));
-        CK(hfd::launch_div(d, m->U1, m->U1, m->U2, hfd::DIV_STAGE, 0.0, 1.0, dt, m->ph, c.lanes, s));
+        CK(hfd::launch_div(dd, m->U1, m->U1, m->U2, hfd::DIV_STAGE, 0.0, 1.0, dt, m->ph, c.lanes, s));
       }
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
@@ -671,8 +762,11 @@ hfd_status hfd_mesh_autotune(hfd_mesh* m, const double* U, void* stream, int32_t
   m->persistent = pick.persistent;
   m->grid = pick.grid;
   m->lanes = pick.lanes;
+  m->dm.div_staged = pick.staged;
   drop_graphs(m);
-  if (choice) { choice[0] = pick.persistent; choice[1] = pick.grid; choice[2] = pick.lanes; }
+  if (choice) {
+    choice[0] = pick.persistent; choice[1] = pick.grid; choice[2] = pick.lanes; choice[3] = pick.staged;
+  }
   return HFD_OK;
 }
 

@@ -17,6 +17,7 @@
 // double or float; the state, the stage combination and the WENO weight ratios are double.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include <type_traits>
@@ -335,7 +336,8 @@ template <typename T>
 __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* __restrict__ sten,
                                           const T* __restrict__ nrm, const T* __restrict__ w5,
                                           const T* __restrict__ w3, const T* __restrict__ Ua,
-                                          T* __restrict__ h, const Phys& ph, unsigned* err) {
+                                          T* __restrict__ h, const Phys& ph, unsigned* err,
+                                          uint8_t* __restrict__ dbg = nullptr) {
   if (e >= Ef) return;
   const T g1 = phys_g1<T>(ph);
   int s[6];
@@ -413,6 +415,7 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
   T wside[2][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) { wside[0][r] = W5L[r]; wside[1][r] = W5R[r]; }
+  unsigned taken = ph.force_branch == 2 ? 0xffu : 0u;   // 3-node branch taken (testing aid)
   if (rough | amb) {
     T u, v, H, c;
     roe_avg(wi, wj, g1, u, v, H, c);
@@ -440,6 +443,7 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
         sensor64(cq[0], cq[1], cq[2], cq[3], cq[4], ph, t, S);
         bool smooth = (t[0] > ph.sens_lo * S) && (t[0] < ph.sens_hi * S);
         if (smooth && ph.force_branch != 2) continue;
+        taken |= 1u << (side * 4 + q);
         const T* w = w3 + (size_t)(9 * side) * Ef + e;
         T c1 = ld_stream(w) * cq[0] + ld_stream(w + Ef) * cq[1] + ld_stream(w + 2 * (size_t)Ef) * cq[2];
         T c2 = ld_stream(w + 3 * (size_t)Ef) * cq[1] + ld_stream(w + 4 * (size_t)Ef) * cq[2] +
@@ -452,6 +456,7 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
       right_apply(u, v, H, c, nx, ny, C, wside[side]);
     }
   }
+  if (dbg) dbg[e] = (uint8_t)taken;
   // positivity (R16): fall back to the end state of that side
   if (!admissible(wside[0]))
 #pragma unroll
@@ -479,8 +484,9 @@ template <typename T>
 __global__ void __launch_bounds__(128, EdgeOcc<T>::kMinBlocks) k_edge(int Ef, int V, const int32_t* __restrict__ sten,
                                               const T* __restrict__ nrm, const T* __restrict__ w5,
                                               const T* __restrict__ w3, const T* __restrict__ Ua,
-                                              T* __restrict__ h, Phys ph, unsigned* err) {
-  edge_body<T>(blockIdx.x * blockDim.x + threadIdx.x, Ef, V, sten, nrm, w5, w3, Ua, h, ph, err);
+                                              T* __restrict__ h, Phys ph, unsigned* err,
+                                              uint8_t* __restrict__ dbg) {
+  edge_body<T>(blockIdx.x * blockDim.x + threadIdx.x, Ef, V, sten, nrm, w5, w3, Ua, h, ph, err, dbg);
 }
 
 // ------------------------------------------------------------------ k_div
@@ -623,6 +629,58 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return ((unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu) != 0x7ffu;
 }
 
+// Combines the lanes' partial sums of vertex r (every lane of the warp must call this: the
+// reduce-scatter shuffles over the whole warp) and writes R = -acc, or the Runge-Kutta stage
+// combination a*Un + b*(Us + dt*R), for the rows this lane holds; flags non-finite values and
+// non-positive densities in the error word.
+template <typename T, int G>
+__device__ __forceinline__ void div_finish(int r, int lane, bool live, T* acc, int V,
+                                           const StageArgs& sa, const int32_t* __restrict__ vmem,
+                                           const unsigned long long* dtbits, double cfl,
+                                           double* dt_last, unsigned* err) {
+  reduce_scatter12<G>(acc, lane);
+  if (!live) return;
+  const double* __restrict__ Us = sa.Us;
+  const double* __restrict__ Un = sa.Un;
+  double* out = sa.out;
+  const int mode = sa.mode;
+  const double a = sa.a, b = sa.b, dt_fixed = sa.dt_fixed;
+  // time step of this vertex's mesh (a batch holds several meshes, each with its own CFL step)
+  const int mem = vmem ? __ldg(vmem + r) : 0;
+  double dt = dt_fixed > 0.0 ? dt_fixed
+               : sa.dt_member ? __ldg(sa.dt_member + mem)
+                              : cfl * __longlong_as_double((long long)dtbits[mem]);
+  if (mode == DIV_STAGE && lane == 0 && dt_last && (r == 0 || (vmem && __ldg(vmem + r - 1) != mem)))
+    dt_last[mem] = dt;
+  // rows held by this lane after the reduce-scatter: base .. base + per - 1
+  int per = G == 1 ? 12 : G == 2 ? 6 : 3;
+  int base = (G >= 2 && (lane & (G / 2)) ? 6 : 0) + (G >= 4 && (lane & (G / 4)) ? 3 : 0);
+  if (G >= 8) {
+    if (lane & 1) { base += 2; per = 1; } else { per = 2; }
+  }
+  unsigned bad = 0;
+#pragma unroll
+  for (int i = 0; i < 12 / (G >= 8 ? 4 : G); ++i) {
+    if (i >= per) break;
+    int k = base + i;
+    double R = -(double)acc[i];
+    size_t idx = (size_t)k * V + r;
+    double o;
+    if (mode == DIV_RESIDUAL) {
+      o = R;
+    } else {
+      // explicit roundings, so that every kernel holding this code (four-launch, staged,
+      // persistent) gives the same bits: one FMA, one multiply, one FMA
+      o = __dmul_rn(b, __fma_rn(dt, R, Us[idx]));
+      if (a != 0.0) o = __fma_rn(a, Un[idx], o);   // the first stage does not read the base state
+    }
+    out[idx] = o;
+    if (!finite_bits(o)) bad |= ERRBIT_NONFINITE;
+    if (mode == DIV_STAGE && k == 0 && !(o > 0.0)) bad |= ERRBIT_POSITIVITY;
+  }
+  if (bad) atomicOr(err, bad);
+}
+
 template <typename T, int G, bool VISC>
 __device__ __forceinline__ void div_body(int gt, int A, int V, int Ef, const int32_t* __restrict__ vptr,
                                          const int32_t* __restrict__ vidx,
@@ -634,11 +692,6 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, int Ef, const int
                                          const StageArgs& sa, const int32_t* __restrict__ vmem,
                                          const unsigned long long* dtbits, double cfl,
                                          double* dt_last, unsigned* err) {
-  const double* __restrict__ Us = sa.Us;
-  const double* __restrict__ Un = sa.Un;
-  double* out = sa.out;
-  const int mode = sa.mode;
-  const double a = sa.a, b = sa.b, dt_fixed = sa.dt_fixed;
   int r = gt / G, lane = gt % G;
   bool live = r < A;
   T acc[12];
@@ -719,40 +772,7 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, int Ef, const int
       edg(j, h0);
     }
   }
-  reduce_scatter12<G>(acc, lane);
-  if (!live) return;
-  // time step of this vertex's mesh (a batch holds several meshes, each with its own CFL step)
-  const int mem = vmem ? __ldg(vmem + r) : 0;
-  double dt = dt_fixed > 0.0 ? dt_fixed
-               : sa.dt_member ? __ldg(sa.dt_member + mem)
-                              : cfl * __longlong_as_double((long long)dtbits[mem]);
-  if (mode == DIV_STAGE && lane == 0 && dt_last && (r == 0 || (vmem && __ldg(vmem + r - 1) != mem)))
-    dt_last[mem] = dt;
-  // rows held by this lane after the reduce-scatter: base .. base + per - 1
-  int per = G == 1 ? 12 : G == 2 ? 6 : 3;
-  int base = (G >= 2 && (lane & (G / 2)) ? 6 : 0) + (G >= 4 && (lane & (G / 4)) ? 3 : 0);
-  if (G >= 8) {
-    if (lane & 1) { base += 2; per = 1; } else { per = 2; }
-  }
-  unsigned bad = 0;
-#pragma unroll
-  for (int i = 0; i < 12 / (G >= 8 ? 4 : G); ++i) {
-    if (i >= per) break;
-    int k = base + i;
-    double R = -(double)acc[i];
-    size_t idx = (size_t)k * V + r;
-    double o;
-    if (mode == DIV_RESIDUAL) {
-      o = R;
-    } else {
-      o = b * (Us[idx] + dt * R);
-      if (a != 0.0) o += a * Un[idx];   // the first stage does not read the base state
-    }
-    out[idx] = o;
-    if (!finite_bits(o)) bad |= ERRBIT_NONFINITE;
-    if (mode == DIV_STAGE && k == 0 && !(o > 0.0)) bad |= ERRBIT_POSITIVITY;
-  }
-  if (bad) atomicOr(err, bad);
+  div_finish<T, G>(r, lane, live, acc, V, sa, vmem, dtbits, cfl, dt_last, err);
 }
 
 // FP32 data: memory-latency bound, so at least 4 resident blocks of 256 threads per SM; FP64
@@ -776,6 +796,273 @@ __global__ void __launch_bounds__(256, DivOcc<T>::kMinBlocks) k_div(int A, int V
                                              double* dt_last, unsigned* err) {
   div_body<T, G, VISC>(blockIdx.x * blockDim.x + threadIdx.x, A, V, Ef, vptr, vidx, eptr, eidx, cv,
                        ce, cvis, FG, FGv, h, sa, vmem, dtbits, cfl, dt_last, err);
+}
+
+// ------------------------------------------------------------------ k_div_staged (FP32 bulk)
+// The FP32 divergence with its streamed operands staged in shared memory by the Tensor Memory
+// Accelerator's 1D bulk copies.  About four fifths of the FP32 divergence's bytes are the
+// per-vertex index and coefficient chunks, contiguous over consecutive vertices.  The kernel
+// is persistent and warp-specialised: each block walks tiles of consecutive active vertices
+// (host-built, so that a tile's chunks fit one stage buffer).  One producer thread keeps up to
+// kStages tiles in flight -- it waits until the consumers have released a stage buffer (its
+// "empty" mbarrier), then copies the tile's row pointers, index chunks and coefficient chunks
+// into it with bulk copies completing on the stage's "full" mbarrier.  Eight consumer warps
+// compute one tile per stage (8 lanes per vertex) and release the buffer warp by warp, so no
+// block-wide barrier couples them and a warp that finishes early starts on the next staged
+// tile.  The flux gathers stay direct loads (they hit L2), and each lane loads the state
+// values of its stage update before its gathers, so that both latencies overlap.  Per vertex
+// the arithmetic, its order and the reduction are those of div_gather_chunked / div_finish
+// with 8 lanes per vertex: results equal the unstaged kernel's at that lane count bit for bit.
+constexpr int kStageG = 8;                                  // lanes per vertex
+constexpr int kStageCW = 8;                                 // consumer warps
+constexpr int kStageThreads = 32 * (kStageCW + 1);          // + one producer warp
+constexpr unsigned kMbarPolls = 1u << 22;                   // bound of an mbarrier wait
+static_assert(kStageCW * 32 / kStageG == kStageTileVerts, "one group of lanes per tile vertex");
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// 1D bulk copy global -> shared, completing `bytes` transactions on `bar` (16-byte aligned
+// addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Bounded wait for the phase of `bar` with parity `parity`; false if the bound ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  for (unsigned i = 0; i < kMbarPolls; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Byte layout of one staged tile: two row-pointer slots (vptr and eptr from the 16-byte aligned
+// vertex pb = r0 & ~3 on), index chunks, vertex coefficient chunks (6 float4 rows), viscous
+// chunks, edge index chunks, edge coefficient chunks (3 float4 rows).
+struct TileLayout {
+  unsigned vi, cv, cz, ei, ce, total;
+};
+__device__ __forceinline__ TileLayout tile_layout(int nvc, int nec, bool visc) {
+  TileLayout L;
+  L.vi = 2u * kStagePtrSlot;
+  L.cv = L.vi + 16u * nvc;
+  L.cz = L.cv + 96u * nvc;
+  L.ei = L.cz + (visc ? 96u * nvc : 0u);
+  L.ce = L.ei + 16u * nec;
+  L.total = L.ce + 48u * nec;
+  return L;
+}
+
+// meta: per tile {r0, r1, c0, nvc} {m0, nec, pb, 0} (first and end vertex, first vertex chunk
+// and count, first edge chunk and count, first vertex of the row-pointer copies)
+template <bool VISC>
+__global__ void __launch_bounds__(kStageThreads) k_div_staged(
+    int A, int V, int Ef, int ntiles, const int4* __restrict__ meta,
+    const int32_t* __restrict__ vptr, const int32_t* __restrict__ vidx,
+    const int32_t* __restrict__ eptr, const int32_t* __restrict__ eidx,
+    const float* __restrict__ cv, const float* __restrict__ ce, const float* __restrict__ cvis,
+    const float* __restrict__ FG, const float* __restrict__ FGv, const float* __restrict__ h,
+    StageArgs sa, const int32_t* __restrict__ vmem, const unsigned long long* dtbits, double cfl,
+    double* dt_last, unsigned* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+  __shared__ int4 smeta[kStages][2];
+  const int warp = threadIdx.x / 32;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], kStageCW);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (warp == kStageCW) {
+    // ---- producer: one thread
+    if (threadIdx.x % 32 != 0) return;
+    int k = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+      const int st = k % kStages, n = k / kStages;
+      if (n > 0 && !mbar_wait(&empty[st], (n - 1) & 1)) {
+        atomicOr(err, ERRBIT_TIMEOUT);
+        return;
+      }
+      const int4 a = __ldg(meta + 2 * t), b = __ldg(meta + 2 * t + 1);
+      smeta[st][0] = a;
+      smeta[st][1] = b;
+      const int nseg = (a.y + 1 - b.z + 3) & ~3;           // row pointers pb .. r1, whole int4s
+      const TileLayout L = tile_layout(a.w, b.y, VISC);
+      unsigned char* buf = smem + st * kStageTileBytes;
+      unsigned long long* bar = &full[st];
+      mbar_expect_tx(bar, 8u * nseg + (L.total - 2u * kStagePtrSlot));
+      bulk_g2s(buf, vptr + b.z, 4u * nseg, bar);
+      bulk_g2s(buf + kStagePtrSlot, eptr + b.z, 4u * nseg, bar);
+      bulk_g2s(buf + L.vi, vidx + 4 * (size_t)a.z, 16u * a.w, bar);
+      bulk_g2s(buf + L.cv, cv + 24 * (size_t)a.z, 96u * a.w, bar);
+      if (VISC) bulk_g2s(buf + L.cz, cvis + 24 * (size_t)a.z, 96u * a.w, bar);
+      if (b.y > 0) {
+        bulk_g2s(buf + L.ei, eidx + 4 * (size_t)b.x, 16u * b.y, bar);
+        bulk_g2s(buf + L.ce, ce + 12 * (size_t)b.x, 48u * b.y, bar);
+      }
+    }
+    return;
+  }
+  // ---- consumers: 8 lanes per vertex, one tile per stage
+  const int ct = threadIdx.x;
+  const int lane = ct % kStageG;
+  const int vloc = ct / kStageG;
+  // rows this lane holds after the 8-lane reduce-scatter (as in div_finish)
+  const int per = (lane & 1) ? 1 : 2;
+  const int base = ((lane & 4) ? 6 : 0) + ((lane & 2) ? 3 : 0) + ((lane & 1) ? 2 : 0);
+  const bool stage_mode = sa.mode == DIV_STAGE;
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int st = k % kStages, n = k / kStages;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[st], n & 1));
+    if (!ok) {                     // a copy that never completed: report it and leave
+      if ((ct & 31) == 0) atomicOr(err, ERRBIT_TIMEOUT);
+      return;
+    }
+    const int4 ma = smeta[st][0], mb = smeta[st][1];
+    const int r0 = ma.x, r1 = ma.y, c0 = ma.z, m0 = mb.x, pb = mb.z;
+    const int r = r0 + vloc;
+    const bool live = r < r1;
+    double us[2] = {0.0, 0.0}, un[2] = {0.0, 0.0};
+    if (live && stage_mode) {      // state values of the stage update, loaded early
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        if (i >= per) break;
+        const size_t idx = (size_t)(base + i) * V + r;
+        us[i] = sa.Us[idx];
+        if (sa.a != 0.0) un[i] = sa.Un[idx];
+      }
+    }
+    const unsigned char* buf = smem + st * kStageTileBytes;
+    const TileLayout L = tile_layout(ma.w, mb.y, VISC);
+    const int* s_vp = reinterpret_cast<const int*>(buf);
+    const int* s_ep = reinterpret_cast<const int*>(buf + kStagePtrSlot);
+    const int4* s_vi = reinterpret_cast<const int4*>(buf + L.vi);
+    const float4* s_cv = reinterpret_cast<const float4*>(buf + L.cv);
+    const float4* s_cz = reinterpret_cast<const float4*>(buf + L.cz);
+    const int4* s_ei = reinterpret_cast<const int4*>(buf + L.ei);
+    const float4* s_ce = reinterpret_cast<const float4*>(buf + L.ce);
+    float acc[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) acc[q] = 0.f;
+    if (live) {
+      const int lc0 = s_vp[r - pb] - c0, nc = s_vp[r + 1 - pb] - c0 - lc0;
+      for (int ch = lane; ch < nc; ch += kStageG) {
+        const int lc = lc0 + ch;
+        const int4 u = s_vi[lc];
+        float4 kk[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) kk[i] = s_cv[6 * lc + i];
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          float f[8];
+          ld8(FG + (size_t)chk_idx(i4c(u, q4), V, err) * 8, f);
+          const float c0f = f4c(kk[0], q4), c0g = f4c(kk[1], q4), cxf = f4c(kk[2], q4);
+          const float cxg = f4c(kk[3], q4), cyf = f4c(kk[4], q4), cyg = f4c(kk[5], q4);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[q] = fmaf(c0g, f[4 + q], fmaf(c0f, f[q], acc[q]));
+            acc[4 + q] = fmaf(cxg, f[4 + q], fmaf(cxf, f[q], acc[4 + q]));
+            acc[8 + q] = fmaf(cyg, f[4 + q], fmaf(cyf, f[q], acc[8 + q]));
+          }
+        }
+        if (VISC) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) kk[i] = s_cz[6 * lc + i];
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            float f[8];
+            ld8(FGv + (size_t)chk_idx(i4c(u, q4), V, err) * 8, f);
+            const float c0f = f4c(kk[0], q4), c0g = f4c(kk[1], q4), cxf = f4c(kk[2], q4);
+            const float cxg = f4c(kk[3], q4), cyf = f4c(kk[4], q4), cyg = f4c(kk[5], q4);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              acc[q] = fmaf(-c0g, f[4 + q], fmaf(-c0f, f[q], acc[q]));
+              acc[4 + q] = fmaf(-cxg, f[4 + q], fmaf(-cxf, f[q], acc[4 + q]));
+              acc[8 + q] = fmaf(-cyg, f[4 + q], fmaf(-cyf, f[q], acc[8 + q]));
+            }
+          }
+        }
+      }
+      const int le0 = s_ep[r - pb] - m0, mc = s_ep[r + 1 - pb] - m0 - le0;
+      for (int ch = lane; ch < mc; ch += kStageG) {
+        const int le = le0 + ch;
+        const int4 e = s_ei[le];
+        const float4 d0 = s_ce[3 * le], dx = s_ce[3 * le + 1], dy = s_ce[3 * le + 2];
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          float hv[4];
+          ld4(h + (size_t)chk_idx(i4c(e, q4), Ef, err) * 4, hv);
+          const float a0 = f4c(d0, q4), ax = f4c(dx, q4), ay = f4c(dy, q4);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[q] = fmaf(a0, hv[q], acc[q]);
+            acc[4 + q] = fmaf(ax, hv[q], acc[4 + q]);
+            acc[8 + q] = fmaf(ay, hv[q], acc[8 + q]);
+          }
+        }
+      }
+    }
+    // this warp is done with the stage buffer
+    __syncwarp();
+    if ((ct & 31) == 0) mbar_arrive(&empty[st]);
+    // combine the 8 lanes and write (the arithmetic of div_finish, on the preloaded state)
+    reduce_scatter12<kStageG>(acc, lane);
+    if (!live) continue;
+    const int mem = vmem ? __ldg(vmem + r) : 0;
+    const double dt = sa.dt_fixed > 0.0 ? sa.dt_fixed
+                      : sa.dt_member ? __ldg(sa.dt_member + mem)
+                                     : cfl * __longlong_as_double((long long)dtbits[mem]);
+    if (stage_mode && lane == 0 && dt_last && (r == 0 || (vmem && __ldg(vmem + r - 1) != mem)))
+      dt_last[mem] = dt;
+    unsigned bad = 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      if (i >= per) break;
+      const int row = base + i;
+      const double R = -(double)acc[i];
+      const size_t idx = (size_t)row * V + r;
+      double o;
+      if (!stage_mode) {
+        o = R;
+      } else {
+        o = __dmul_rn(sa.b, __fma_rn(dt, R, us[i]));
+        if (sa.a != 0.0) o = __fma_rn(sa.a, un[i], o);
+      }
+      sa.out[idx] = o;
+      if (!finite_bits(o)) bad |= ERRBIT_NONFINITE;
+      if (stage_mode && row == 0 && !(o > 0.0)) bad |= ERRBIT_POSITIVITY;
+    }
+    if (bad) atomicOr(err, bad);
+  }
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -1011,10 +1298,11 @@ cudaError_t launch_edge(const DevMesh& m, const Phys& ph, cudaStream_t s) {
   if (m.precision == 0)
     k_edge<double><<<nb, 128, 0, s>>>(m.Ef, m.V, m.sten, (const double*)m.nrm, (const double*)m.w5,
                                       (const double*)m.w3, (const double*)m.Ua, (double*)m.h, ph,
-                                      m.err);
+                                      m.err, m.dbg_branch);
   else
     k_edge<float><<<nb, 128, 0, s>>>(m.Ef, m.V, m.sten, (const float*)m.nrm, (const float*)m.w5,
-                                     (const float*)m.w3, (const float*)m.Ua, (float*)m.h, ph, m.err);
+                                     (const float*)m.w3, (const float*)m.Ua, (float*)m.h, ph, m.err,
+                                     m.dbg_branch);
   return cudaGetLastError();
 }
 
@@ -1034,6 +1322,33 @@ static void div_dispatch(const DevMesh& m, const StageArgs& sa, const Phys& ph, 
                                           m.dt_last, m.err);
 }
 
+// Staged FP32 divergence: a persistent grid of every co-resident block (kStages stage buffers
+// of dynamic shared memory each), at most one block per tile.
+template <bool VISC>
+static cudaError_t div_staged_launch(const DevMesh& m, const StageArgs& sa, const Phys& ph,
+                                     cudaStream_t s) {
+  static int per_sm[2] = {0, 0}, nsm = 0;            // per process; one GPU model per process
+  const int smem = kStages * kStageTileBytes;
+  if (!per_sm[VISC]) {
+    cudaError_t e = cudaFuncSetAttribute(k_div_staged<VISC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int b = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_div_staged<VISC>, kStageThreads, smem);
+    if (e != cudaSuccess) return e;
+    per_sm[VISC] = b > 0 ? b : 1;
+  }
+  const int grid = (int)std::min<long long>((long long)per_sm[VISC] * nsm, m.ntiles);
+  k_div_staged<VISC><<<grid, kStageThreads, smem, s>>>(
+      m.A, m.V, m.Ef, m.ntiles, reinterpret_cast<const int4*>(m.tiles), m.vptr, m.vidx, m.eptr,
+      m.eidx, (const float*)m.cv, (const float*)m.ce, (const float*)m.cvis, (const float*)m.FG,
+      (const float*)m.FGv, (const float*)m.h, sa, m.vmem, m.dtbits, ph.cfl, m.dt_last, m.err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, double* out, int mode,
                        double a, double b, double dt_fixed, const Phys& ph, int lanes,
                        cudaStream_t s, const double* dt_member) {
@@ -1046,6 +1361,8 @@ cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, dou
       case 8: div_dispatch<double, 8>(m, sa, ph, s); break;
       default: div_dispatch<double, 4>(m, sa, ph, s); break;
     }
+  } else if (m.div_staged && m.ntiles > 0) {
+    return m.viscous ? div_staged_launch<true>(m, sa, ph, s) : div_staged_launch<false>(m, sa, ph, s);
   } else {
     switch (lanes) {
       case 1: div_dispatch<float, 1>(m, sa, ph, s); break;

@@ -41,6 +41,13 @@ template <> __host__ __device__ inline float phys_half_inv_harten<float>(const P
 
 // Divergence entries per chunk of the FP32-bulk layout (vector loads of 4 coefficients).
 constexpr int kDivChunk = 4;
+// Staged FP32 divergence: vertices per tile, stage buffers per block, bytes of one stage buffer
+// (two row-pointer slots of kStagePtrSlot bytes, then per chunk: vertex indices 16 B, vertex
+// coefficients 96 B (+96 B viscous), edge indices 16 B, edge coefficients 48 B).
+constexpr int kStageTileVerts = 32;
+constexpr int kStages = 3;
+constexpr int kStageTileBytes = 36 * 1024;
+constexpr int kStagePtrSlot = 160;     // 36 row pointers of a tile (pb .. r1, whole int4s) + slack
 
 // Device arrays of one mesh in internal numbering.  Coefficient and flux arrays hold elements
 // of the path's bulk precision T (double or float), addressed through void pointers here.
@@ -66,6 +73,12 @@ struct DevMesh {
   void* cv = nullptr;
   void* ce = nullptr;
   void* cvis = nullptr;  // viscous rows, same layout as cv
+  // FP32 bulk: tiles of consecutive active vertices for the staged divergence (8 int32 per
+  // tile: {r0, r1, c0, nvc, m0, nec, pb, 0}; a tile's chunks fit one stage buffer), and whether
+  // launch_div uses that kernel (1) or the unstaged one with the mesh's lane count (0)
+  int32_t* tiles = nullptr;
+  int ntiles = 0;
+  int div_staged = 0;
   // ghosts
   int32_t *gid = nullptr, *gdonor = nullptr, *gflags = nullptr;
   // time step
@@ -81,6 +94,9 @@ struct DevMesh {
   // scratch: AoS copies of the state [V][12], vertex fluxes [V][8] (+ viscous), edge fluxes [Ef][4]
   void* Ua = nullptr;
   void* FG = nullptr;
+  // testing aid: when set, k_edge writes per flux edge the Alg. 1 branch it took (bit side*4+q
+  // set: the WENO-weighted 3-node value of characteristic component q on side L (0) or R (1))
+  uint8_t* dbg_branch = nullptr;
   void* FGv = nullptr;
   void* h = nullptr;
 };

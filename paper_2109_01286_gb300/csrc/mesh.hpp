@@ -35,6 +35,7 @@ struct hfd_mesh {
   int persistent = 0;                   // 1: one cooperative launch per RK stage
   int grid = 0;                         // blocks of the persistent launch (0: all resident)
   std::vector<int32_t> perm;            // internal -> input
+  std::vector<int32_t> fperm;           // internal flux edge -> the prep's flux-edge index
   int32_t* dperm = nullptr;             // device copy of perm
   double* U1 = nullptr;                 // stage buffers 12 x V
   double* U2 = nullptr;

@@ -32,7 +32,8 @@ EXPORTED = ["hfd_default_options", "hfd_last_error", "hfd_prep_create", "hfd_pre
             "hfd_last_dt", "hfd_check", "hfd_steps_profiled", "hfd_residual_static",
             "hfd_prep_concat", "hfd_mesh_set_launch", "hfd_mesh_set_lanes", "hfd_mesh_autotune",
             "hfd_mesh_set_barrier_limit", "hfd_adjoint", "hfd_batch_create", "hfd_batch_destroy",
-            "hfd_batch_mesh", "hfd_batch_step"]
+            "hfd_batch_mesh", "hfd_batch_step", "hfd_measure_fma_peaks",
+            "hfd_mesh_set_div_staged", "hfd_edge_branches"]
 
 
 class HfdError(RuntimeError):
@@ -124,6 +125,8 @@ _lib.hfd_mesh_set_launch.argtypes = [_P, ctypes.c_int32, ctypes.c_int32]
 _lib.hfd_mesh_autotune.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int32)]
 _lib.hfd_mesh_set_barrier_limit.argtypes = [_P, ctypes.c_uint32]
 _lib.hfd_mesh_set_lanes.argtypes = [_P, ctypes.c_int32]
+_lib.hfd_mesh_set_div_staged.argtypes = [_P, ctypes.c_int32]
+_lib.hfd_edge_branches.argtypes = [_P, _P, _P, _P]
 _lib.hfd_adjoint.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
 _lib.hfd_step.argtypes = [_P, _P, ctypes.c_double, _P]
 _lib.hfd_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32,
@@ -132,6 +135,9 @@ _lib.hfd_batch_destroy.argtypes = [_P]
 _lib.hfd_batch_mesh.argtypes = [_P, ctypes.POINTER(_P)]
 _lib.hfd_batch_step.argtypes = [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double), _P]
 _lib.hfd_steps.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int32, _P]
+_lib.hfd_measure_fma_peaks.argtypes = [ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int32), _P]
 _lib.hfd_steps_host.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_int32, _P]
 _lib.hfd_last_dt.argtypes = [_P, _P, _P]
 _lib.hfd_check.argtypes = [_P, _P]
@@ -257,6 +263,15 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
+def measure_fma_peaks(stream=None):
+    """hfd_measure_fma_peaks: measured FP64 and FP32 FMA throughput of the current device in
+    FLOP/s, and its SM count."""
+    f64, f32, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _ok(_lib.hfd_measure_fma_peaks(ctypes.byref(f64), ctypes.byref(f32), ctypes.byref(sms),
+                                   _stream(stream)), "hfd_measure_fma_peaks")
+    return {"fp64_flops": f64.value, "fp32_flops": f32.value, "sm_count": sms.value}
+
+
 def _dptr(t):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
@@ -275,6 +290,8 @@ class Mesh:
             pr = {None: -1, "fp64": 0, "fp32": 1, "mixed": 1, 0: 0, 1: 1}[precision]
             _ok(_lib.hfd_mesh_upload(prep._h, pr, ctypes.byref(h)), "hfd_mesh_upload")
         else:
+            if precision is not None:
+                opts["precision"] = precision
             self.options = options(**opts)
             d, keep = _desc(mesh)
             _ok(_lib.hfd_mesh_create(ctypes.byref(d), ctypes.byref(self.options), ctypes.byref(h)),
@@ -366,10 +383,22 @@ class Mesh:
 
     def autotune(self, U, stream=None):
         """Pick the fastest launch shape for one RK stage on state U; returns
-        (persistent, grid, lanes)."""
-        c = (ctypes.c_int32 * 3)()
+        (persistent, grid, lanes, staged)."""
+        c = (ctypes.c_int32 * 4)()
         _ok(_lib.hfd_mesh_autotune(self._h, _dptr(U), _stream(stream), c), "hfd_mesh_autotune")
-        return int(c[0]), int(c[1]), int(c[2])
+        return int(c[0]), int(c[1]), int(c[2]), int(c[3])
+
+    def edge_branches(self, U, stream=None):
+        """hfd_edge_branches: per flux edge (the preprocessing's flux-edge order) the byte of
+        Alg. 1 branches taken on state U (bit side*4+q: the 3-node WENO value)."""
+        out = np.zeros(int(self.stats.nflux_edges), dtype=np.uint8)
+        _ok(_lib.hfd_edge_branches(self._h, _dptr(U), out.ctypes.data_as(ctypes.c_void_p),
+                                   _stream(stream)), "hfd_edge_branches")
+        return out
+
+    def set_div_staged(self, staged):
+        """hfd_mesh_set_div_staged: the staged FP32 divergence (1) or the unstaged one (0)."""
+        _ok(_lib.hfd_mesh_set_div_staged(self._h, int(staged)), "hfd_mesh_set_div_staged")
 
     def last_dt(self, stream=None):
         """dt of the last step: a float, or one value per member for a batch."""

@@ -38,6 +38,53 @@ def inject_oracle_coefficients(prep, P, V):
         prep.set(k, v)
 
 
+def oracle_with_library_coefficients(P, prep):
+    """The oracle's preprocessing with the library's own geometry coefficients put in (5-node
+    and 3-node weights, divergence and viscous rows), after checking that both sides made the
+    same discrete choices.  The oracle's residual on it is the method's arithmetic on exactly
+    the coefficients the library's full path uses."""
+    import copy
+    assert np.array_equal(prep.get("flux_edges"), P.edges)
+    assert np.array_equal(prep.get("stencil").reshape(-1, 6), P.stencil)
+    assert np.array_equal(prep.get("active"), P.active)
+    Q = copy.copy(P)
+    Q.w5 = prep.get("w5").reshape(P.w5.shape).copy()
+    Q.w3 = prep.get("w3").reshape(P.w3.shape).copy()
+
+    def put(mats, flat):
+        out = []
+        off = 0
+        n = len(P.active)
+        ms = [d.tocsr().copy() for d in mats]
+        for d in ms:
+            d.sort_indices()
+        for r in range(n):
+            for d in ms:
+                a, b = d.indptr[r], d.indptr[r + 1]
+                d.data[a:b] = flat[off:off + (b - a)]
+                off += b - a
+        assert off == len(flat)
+        return ms
+    Q.D = put(P.D, prep.get("div_coef"))
+    if getattr(P, "Dv", None) is not None:
+        Q.Dv = put(P.Dv, prep.get("visc_coef"))
+    return Q
+
+
+def elementwise_rel(R, R_ref, cols=None):
+    """Largest |R - R_ref| / (|R_ref| + rms of R_ref over the entry's row group) over every
+    entry: an element-wise bound with a floor, so that no single vertex can hide under a norm,
+    while entries near a zero of the residual are measured against their group's scale."""
+    if cols is not None:
+        R, R_ref = R[:, cols], R_ref[:, cols]
+    worst = 0.0
+    for g in range(3):
+        a, b = R[4 * g:4 * g + 4], R_ref[4 * g:4 * g + 4]
+        floor = np.sqrt(np.mean(b * b))
+        worst = max(worst, float(np.max(np.abs(a - b) / (np.abs(b) + floor))))
+    return worst
+
+
 def rel_l2_groups(R, R_ref, cols=None):
     """Relative L2 error of the w, w_x and w_y row groups (rows 0-3, 4-7, 8-11)."""
     if cols is not None:
@@ -108,3 +155,42 @@ def run_checked_build_cases(pkg, torch):
         out[name + "/U"] = mesh.export_state(X).cpu().numpy()
         mesh.check()
     return out
+
+
+def c2_chunk_oracle_residual(task):
+    """Spawned worker: the oracle residual of the n x n four-quadrant mesh (5 ghost layers) at a
+    chunk of active vertices, with the library's own coefficients for that chunk (loaded from the
+    .npz of its preprocessing arrays), and the chunk's vertices that read an edge whose sensor
+    lies within 1e-9 of a threshold.  Returns (chunk, R[:, chunk], near-threshold vertices)."""
+    import synth
+    n, chunk, lib_path = task
+    lib = np.load(lib_path)
+    m = synth.jittered_box_with_ghosts(n, n, (0.0, 1.0), (0.0, 1.0), 5, seed=2)
+    U = synth.four_quadrant(m)
+    P = oracle.prepare(m, active=chunk)
+    fe = lib["flux_edges"]
+    pos = np.searchsorted(fe, P.edges)
+    assert np.array_equal(fe[pos], P.edges)
+    assert np.array_equal(lib["stencil"].reshape(-1, 6)[pos], P.stencil)
+    P.w5 = lib["w5"].reshape(-1, 2, 15)[pos].copy()
+    P.w3 = lib["w3"].reshape(-1, 2, 3, 3)[pos].copy()
+    act = lib["active"]
+    rl = np.searchsorted(act, chunk)
+    assert np.array_equal(act[rl], chunk)
+    N = np.diff(lib["div_vptr"])
+    M = np.diff(lib["div_eptr"])
+    off = np.concatenate([[0], np.cumsum(3 * (2 * N + M))])
+    D = [d.tocsr().copy() for d in P.D]
+    for d in D:
+        d.sort_indices()
+    for i, r in enumerate(rl):
+        L = 2 * N[r] + M[r]
+        blk = lib["div_coef"][off[r]:off[r] + 3 * L]
+        for k, d in enumerate(D):
+            a, b = d.indptr[i], d.indptr[i + 1]
+            assert b - a == L
+            d.data[a:b] = blk[k * L:(k + 1) * L]
+    P.D = D
+    R = oracle.residual(m, P, U.copy())
+    bad = near_threshold_vertices(m, P, U, P.opts)
+    return chunk, R[:, chunk], bad

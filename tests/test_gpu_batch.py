@@ -104,8 +104,8 @@ def test_persistent_launch_equals_four_launch_stage(members, precision):
     torch.cuda.synchronize()
     batch.check()
     assert (torch.linalg.norm(a - b) / torch.linalg.norm(a)).item() < tol
-    persistent, grid, lanes = batch.autotune(_state(batch, Ub))
-    assert persistent in (0, 1) and lanes in (1, 2, 4, 8)
+    persistent, grid, lanes, staged = batch.autotune(_state(batch, Ub))
+    assert persistent in (0, 1) and lanes in (1, 2, 4, 8) and staged in (0, 1)
     c = _state(batch, Ub)
     batch.steps(c, 0.0, 2)
     torch.cuda.synchronize()

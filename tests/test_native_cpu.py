@@ -92,6 +92,31 @@ def test_host_prep_coefficients_match_oracle(c1):
     assert d.max() < 1e-6
 
 
+def test_host_prep_five_node_gaps_follow_from_conditioning(c1):
+    """The library's 5-node weights (one-sided Jacobi SVD) and the oracle's (LAPACK) are two
+    backward-stable evaluations of a truncated pseudo-inverse (Sec. 2.2, R3).  Its first-order
+    sensitivity to a relative perturbation eps of the 15x15 system is eps * sigma_max /
+    sigma_kept (the dropped singular value is the structural zero of the squared conic), so on
+    every edge side the two must agree to within a small multiple of that bound: the gaps of up
+    to ~1e-7 are the stencils' conditioning, not an error of either side."""
+    m, P, prep = c1
+    from oracle import hfd_oracle as H
+    wl = prep.get("w5").reshape(-1, 2, 15)
+    worst = 0.0
+    for i, e in enumerate(P.edges):
+        ids, rel, ell, n = H.edge_geometry(m, P.topo, int(e))
+        for side, five in enumerate([H.LEFT5, H.RIGHT5]):
+            X = rel[five] / ell
+            p, px, py = H.taylor_basis(X[:, 0], X[:, 1], 4)
+            A = np.zeros((15, 15))
+            A[0::3], A[1::3], A[2::3] = p.T, px.T, py.T
+            S = np.linalg.svd(A, compute_uv=False)
+            kappa = S[0] / S[P.rank[i, side] - 1]
+            gap = np.abs(wl[i, side] - P.w5[i, side]).max()
+            worst = max(worst, gap / (np.finfo(float).eps * kappa))
+    assert worst < 4.0, worst
+
+
 @pytest.mark.parametrize("n", [16, 24])
 def test_host_prep_viscous_rows_match_oracle(pkg, n):
     m = synth.jittered_grid(n, n, 2 * np.pi, 2 * np.pi, seed=3)
