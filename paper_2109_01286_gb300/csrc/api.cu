@@ -230,6 +230,7 @@ hfd_status upload_streams(hfd_mesh* m, const hfd::Prep& P, const std::vector<int
   TRY(dev_alloc(m, &d.FG, V * 8 * sizeof(T)));
   if (P.opts.viscous) TRY(dev_alloc(m, &d.FGv, V * 8 * sizeof(T)));
   TRY(dev_alloc(m, &d.h, (size_t)Ef * 4 * sizeof(T)));
+  if (std::is_same<T, float>::value) TRY(dev_alloc(m, (void**)&d.wref, 4 * sizeof(float)));
   return HFD_OK;
 }
 

@@ -226,6 +226,104 @@ __device__ __forceinline__ void rusanov_flux(const T* wl, const T* wr, T nx, T n
   for (int i = 0; i < 4; ++i) hq[i] = T(0.5) * (fl[i] + fr[i]) - T(0.5) * s * (wr[i] - wl[i]);
 }
 
+// ---- FP32 bulk in deviations from a reference state.  At low Mach number the pressure and
+// energy dwarf the flow's variations (Mach 0.1: p ~ 71 against O(1) changes), and FP32 fluxes
+// formed from full states lose those variations to rounding.  The FP32 path therefore carries
+// the state copy as deviations d = w - w0 from a reference state w0 (vertex 0's state at the
+// stage input, rounded to floats; the deviation is formed in FP64) and every flux as its
+// deviation F(w) - F(w0).  Each least-squares divergence row annihilates constant fluxes, so the
+// divergence is unchanged, and the deviations are formed by exact algebra on d:
+//   u - u0 = (d1 - u0 d0) / rho,  p - p0 = (gamma-1) (d3 - (m0 du + d1 u + n0 dv + d2 v) / 2),
+//   (rho u_n) - (rho u_n)0 = rho0 du_n + d0 u_n,  (m u_n + p n_x) - (...)0 = m0 du_n + d1 u_n + dp n_x,
+//   ((E + p) u_n) - (...)0 = (E0 + p0) du_n + (d3 + dp) u_n,
+// so no full-size quantity is subtracted in FP32.
+struct Ref0 {
+  float rho, m, n, E, u, v, p;
+};
+__device__ __forceinline__ Ref0 make_ref(const float* w0, float g1) {
+  Ref0 r;
+  r.rho = w0[0]; r.m = w0[1]; r.n = w0[2]; r.E = w0[3];
+  const float ir = 1.0f / r.rho;
+  r.u = r.m * ir; r.v = r.n * ir;
+  r.p = g1 * (r.E - 0.5f * (r.m * r.u + r.n * r.v));
+  return r;
+}
+// primitive deviations of the state w0 + d: density, velocity and their deviations, pressure
+// deviation
+struct Dev {
+  float rho, ir, du, dv, u, v, dp;
+};
+__device__ __forceinline__ Dev make_dev(const Ref0& r, const float* d, float g1) {
+  Dev q;
+  q.rho = r.rho + d[0];
+  q.ir = 1.0f / q.rho;
+  q.du = (d[1] - r.u * d[0]) * q.ir;
+  q.dv = (d[2] - r.v * d[0]) * q.ir;
+  q.u = r.u + q.du;
+  q.v = r.v + q.dv;
+  q.dp = g1 * (d[3] - 0.5f * (r.m * q.du + d[1] * q.u + r.n * q.dv + d[2] * q.v));
+  return q;
+}
+// F_n(w0 + d) - F_n(w0) along (nx, ny)
+__device__ __forceinline__ void normal_flux_dev(const Ref0& r, const Dev& q, const float* d, float nx,
+                                                float ny, float* f) {
+  const float un = q.u * nx + q.v * ny, dun = q.du * nx + q.dv * ny;
+  f[0] = r.rho * dun + d[0] * un;
+  f[1] = r.m * dun + d[1] * un + q.dp * nx;
+  f[2] = r.n * dun + d[2] * un + q.dp * ny;
+  f[3] = (r.E + r.p) * dun + (d[3] + q.dp) * un;
+}
+// Roe's flux with Harten's fix (as roe_flux) minus F_n(w0), from the two sides' deviations dl,
+// dr: the averages use the full states, every jump the deviations.
+__device__ __forceinline__ void roe_flux_dev(const Ref0& r, const float* dl, const float* dr,
+                                             float nx, float ny, float g1, float harten,
+                                             float half_inv_harten, float* hq) {
+  const Dev L = make_dev(r, dl, g1), R = make_dev(r, dr, g1);
+  const float sl = sqrtf(L.rho), sr = sqrtf(R.rho);
+  const float Hl = (r.E + dl[3] + r.p + L.dp) * L.ir, Hr = (r.E + dr[3] + r.p + R.dp) * R.ir;
+  const float fl_ = sl / (sl + sr), fr_ = 1.0f - fl_;
+  const float u = fl_ * L.u + fr_ * R.u, v = fl_ * L.v + fr_ * R.v, H = fl_ * Hl + fr_ * Hr;
+  const float c2 = g1 * (H - 0.5f * (u * u + v * v));
+  const float ic = rsqrtf(c2), c = c2 * ic;
+  const float qn = u * nx + v * ny;
+  const float rho = sl * sr, dp = R.dp - L.dp, drho = dr[0] - dl[0];
+  const float dux = R.du - L.du, dvy = R.dv - L.dv;
+  const float dun = dux * nx + dvy * ny, dut = dvy * nx - dux * ny;
+  const float ic2 = ic * ic, hc2 = 0.5f * ic2, qc2 = 0.25f * ic2;
+  const float rcd = rho * c * dun;
+  const float a[4] = {(dp - rcd) * qc2, 0.5f * drho - dp * hc2, (0.5f * rho) * dut, (dp + rcd) * qc2};
+  const float lam[4] = {qn - c, qn, qn, qn + c};
+  const float del = harten * c, i2del = half_inv_harten * ic;
+  float k[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float al = fabsf(lam[i]);
+    if (al < del) al = (lam[i] * lam[i] + del * del) * i2del;
+    k[i] = al * a[i];
+  }
+  float diss[4];
+  right_apply(u, v, H, c, nx, ny, k, diss);
+  float fl[4], fr[4];
+  normal_flux_dev(r, L, dl, nx, ny, fl);
+  normal_flux_dev(r, R, dr, nx, ny, fr);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) hq[i] = 0.5f * (fl[i] + fr[i]) - diss[i];
+}
+// Rusanov's flux (as rusanov_flux) minus F_n(w0), from deviations.
+__device__ __forceinline__ void rusanov_flux_dev(const Ref0& r, const float* dl, const float* dr,
+                                                 float nx, float ny, float g1, float* hq) {
+  const Dev L = make_dev(r, dl, g1), R = make_dev(r, dr, g1);
+  const float gam = g1 + 1.0f;
+  const float sl = fabsf(L.u * nx + L.v * ny) + sqrtf(gam * (r.p + L.dp) * L.ir);
+  const float sr = fabsf(R.u * nx + R.v * ny) + sqrtf(gam * (r.p + R.dp) * R.ir);
+  const float s = sl >= sr ? sl : sr;
+  float fl[4], fr[4];
+  normal_flux_dev(r, L, dl, nx, ny, fl);
+  normal_flux_dev(r, R, dr, nx, ny, fr);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) hq[i] = 0.5f * (fl[i] + fr[i]) - 0.5f * s * (dr[i] - dl[i]);
+}
+
 // rho > 0 and p > 0 (R16), without a division: p = (gamma-1)(E - |m|^2/(2 rho)) has the sign
 // of E rho - |m|^2/2 when rho > 0.
 template <typename T>
@@ -249,26 +347,52 @@ __device__ __forceinline__ void smoothness(T u0, T u1, T u2, T u3, T u4, T* b) {
 // ------------------------------------------------------------------ k_vertex
 template <typename T, bool VISC>
 __device__ __forceinline__ void vertex_body(int v, int V, const double* __restrict__ U, T* Ua,
-                                            T* FG, T* FGv, const Phys& ph) {
+                                            T* FG, T* FGv, const Phys& ph, float* wref,
+                                            const float* s0f, const double* s0d) {
   if (v >= V) return;
   double w[12];
 #pragma unroll
   for (int r = 0; r < 12; ++r) w[r] = U[(size_t)r * V + v];
   T* ua = Ua + (size_t)v * 12;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    T t[4] = {T(w[4 * i]), T(w[4 * i + 1]), T(w[4 * i + 2]), T(w[4 * i + 3])};
-    st4(ua + 4 * i, t);
-  }
   T g1 = phys_g1<T>(ph);
-  T q[4] = {T(w[0]), T(w[1]), T(w[2]), T(w[3])};
-  T ir = T(1) / q[0];
-  T u = q[1] * ir, vv = q[2] * ir;
-  T p = pressure(q, g1);
-  T F[4] = {q[1], q[1] * u + p, q[2] * u, (q[3] + p) * u};
-  T Gf[4] = {q[2], q[1] * vv, q[2] * vv + p, (q[3] + p) * vv};
-  st4(FG + (size_t)v * 8, F);
-  st4(FG + (size_t)v * 8 + 4, Gf);
+  if constexpr (std::is_same<T, float>::value) {
+    // deviations from the reference state (vertex 0 at the stage input, rounded to floats;
+    // s0f / s0d hold it as floats and as their exact doubles, formed once per block)
+    float w0[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) w0[r] = s0f[r];
+    if (v == 0 && wref) st4(wref, w0);
+    float d[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) d[r] = (float)(w[r] - s0d[r]);
+    st4(ua, d);
+#pragma unroll
+    for (int i = 1; i < 3; ++i) {
+      float t[4] = {(float)w[4 * i], (float)w[4 * i + 1], (float)w[4 * i + 2], (float)w[4 * i + 3]};
+      st4(ua + 4 * i, t);
+    }
+    const Ref0 r0 = make_ref(w0, g1);
+    const Dev q = make_dev(r0, d, g1);
+    float F[4], Gf[4];
+    normal_flux_dev(r0, q, d, 1.0f, 0.0f, F);
+    normal_flux_dev(r0, q, d, 0.0f, 1.0f, Gf);
+    st4(FG + (size_t)v * 8, F);
+    st4(FG + (size_t)v * 8 + 4, Gf);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T t[4] = {T(w[4 * i]), T(w[4 * i + 1]), T(w[4 * i + 2]), T(w[4 * i + 3])};
+      st4(ua + 4 * i, t);
+    }
+    T q[4] = {T(w[0]), T(w[1]), T(w[2]), T(w[3])};
+    T ir = T(1) / q[0];
+    T u = q[1] * ir, vv = q[2] * ir;
+    T p = pressure(q, g1);
+    T F[4] = {q[1], q[1] * u + p, q[2] * u, (q[3] + p) * u};
+    T Gf[4] = {q[2], q[1] * vv, q[2] * vv + p, (q[3] + p) * vv};
+    st4(FG + (size_t)v * 8, F);
+    st4(FG + (size_t)v * 8 + 4, Gf);
+  }
   if (VISC) {   // viscous flux from w, w_x, w_y (Sec. 2.3; chain rule for the primitives)
     double rho = w[0], uu = w[1] / rho, vw = w[2] / rho;
     double gm = ph.gamma - 1.0;
@@ -291,10 +415,25 @@ __device__ __forceinline__ void vertex_body(int v, int V, const double* __restri
   }
 }
 
+// The FP32 path's reference state for this block: vertex 0's values at the stage input rounded
+// to floats, and those floats as exact doubles (threads 0-3 of the block convert them once).
+__device__ __forceinline__ void block_reference(const double* __restrict__ U, int V, float* s0f,
+                                                double* s0d) {
+  if (threadIdx.x < 4 && V > 0) {
+    const float f = (float)U[(size_t)threadIdx.x * V];
+    s0f[threadIdx.x] = f;
+    s0d[threadIdx.x] = (double)f;
+  }
+  __syncthreads();
+}
+
 template <typename T, bool VISC>
 __global__ void __launch_bounds__(256) k_vertex(int V, const double* __restrict__ U, T* Ua, T* FG,
-                                                T* FGv, Phys ph) {
-  vertex_body<T, VISC>(blockIdx.x * blockDim.x + threadIdx.x, V, U, Ua, FG, FGv, ph);
+                                                T* FGv, Phys ph, float* wref) {
+  __shared__ float s0f[4];
+  __shared__ double s0d[4];
+  if constexpr (std::is_same<T, float>::value) block_reference(U, V, s0f, s0d);
+  vertex_body<T, VISC>(blockIdx.x * blockDim.x + threadIdx.x, V, U, Ua, FG, FGv, ph, wref, s0f, s0d);
 }
 
 // ------------------------------------------------------------------ k_edge
@@ -337,7 +476,7 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
                                           const T* __restrict__ nrm, const T* __restrict__ w5,
                                           const T* __restrict__ w3, const T* __restrict__ Ua,
                                           T* __restrict__ h, const Phys& ph, unsigned* err,
-                                          uint8_t* __restrict__ dbg = nullptr) {
+                                          uint8_t* __restrict__ dbg, const float* __restrict__ wref) {
   if (e >= Ef) return;
   const T g1 = phys_g1<T>(ph);
   int s[6];
@@ -352,11 +491,24 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
     ld12(Ua + (size_t)s[3] * 12, a);
     wj[0] = a[0]; wj[1] = a[1]; wj[2] = a[2]; wj[3] = a[3];
   }
+  // FP32 data are deviations from the reference state w0: the averages and the admissibility
+  // test take the full states w0 + d (FP64 data are the states)
+  float w0[4] = {0.f, 0.f, 0.f, 0.f};
+  T fwi[4], fwj[4];
+  if constexpr (std::is_same<T, float>::value) {
+    const float4 r = __ldg(reinterpret_cast<const float4*>(wref));
+    w0[0] = r.x; w0[1] = r.y; w0[2] = r.z; w0[3] = r.w;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { fwi[q] = w0[q] + wi[q]; fwj[q] = w0[q] + wj[q]; }
+  } else {          // FP64 data are the states themselves (no additions on the FP64 pipe)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { fwi[q] = wi[q]; fwj[q] = wj[q]; }
+  }
   // FP32 left eigenvectors at the Roe state of the edge ends (sensor only)
   float Lf[4][4];
   {
-    float fi[4] = {(float)wi[0], (float)wi[1], (float)wi[2], (float)wi[3]};
-    float fj[4] = {(float)wj[0], (float)wj[1], (float)wj[2], (float)wj[3]};
+    float fi[4] = {(float)fwi[0], (float)fwi[1], (float)fwi[2], (float)fwi[3]};
+    float fj[4] = {(float)fwj[0], (float)fwj[1], (float)fwj[2], (float)fwj[3]};
     float u, v, H, c;
     roe_avg(fi, fj, (float)g1, u, v, H, c);
     left_ev(u, v, c, (float)nx, (float)ny, (float)g1, Lf);
@@ -418,7 +570,7 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
   unsigned taken = ph.force_branch == 2 ? 0xffu : 0u;   // 3-node branch taken (testing aid)
   if (rough | amb) {
     T u, v, H, c;
-    roe_avg(wi, wj, g1, u, v, H, c);
+    roe_avg(fwi, fwj, g1, u, v, H, c);
     T L[4][4];
     left_ev(u, v, c, nx, ny, g1, L);
 #pragma unroll
@@ -458,17 +610,39 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
   }
   if (dbg) dbg[e] = (uint8_t)taken;
   // positivity (R16): fall back to the end state of that side
-  if (!admissible(wside[0]))
+  {
+    T fl[4], fr[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) wside[0][q] = wi[q];
-  if (!admissible(wside[1]))
+    for (int q = 0; q < 4; ++q) {
+      if constexpr (std::is_same<T, float>::value) {
+        fl[q] = w0[q] + wside[0][q];
+        fr[q] = w0[q] + wside[1][q];
+      } else {
+        fl[q] = wside[0][q];
+        fr[q] = wside[1][q];
+      }
+    }
+    if (!admissible(fl))
 #pragma unroll
-    for (int q = 0; q < 4; ++q) wside[1][q] = wj[q];
+      for (int q = 0; q < 4; ++q) wside[0][q] = wi[q];
+    if (!admissible(fr))
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wside[1][q] = wj[q];
+  }
   T hq[4];
-  if (ph.flux == 1)
-    rusanov_flux(wside[0], wside[1], nx, ny, g1, hq);
-  else
-    roe_flux(wside[0], wside[1], nx, ny, g1, phys_harten<T>(ph), phys_half_inv_harten<T>(ph), hq);
+  if constexpr (std::is_same<T, float>::value) {
+    // the flux's deviation from F_n(w0)
+    const Ref0 r0 = make_ref(w0, g1);
+    if (ph.flux == 1)
+      rusanov_flux_dev(r0, wside[0], wside[1], nx, ny, g1, hq);
+    else
+      roe_flux_dev(r0, wside[0], wside[1], nx, ny, g1, phys_harten<T>(ph), phys_half_inv_harten<T>(ph), hq);
+  } else {
+    if (ph.flux == 1)
+      rusanov_flux(wside[0], wside[1], nx, ny, g1, hq);
+    else
+      roe_flux(wside[0], wside[1], nx, ny, g1, phys_harten<T>(ph), phys_half_inv_harten<T>(ph), hq);
+  }
   st4(h + (size_t)e * 4, hq);
 }
 
@@ -485,8 +659,9 @@ __global__ void __launch_bounds__(128, EdgeOcc<T>::kMinBlocks) k_edge(int Ef, in
                                               const T* __restrict__ nrm, const T* __restrict__ w5,
                                               const T* __restrict__ w3, const T* __restrict__ Ua,
                                               T* __restrict__ h, Phys ph, unsigned* err,
-                                              uint8_t* __restrict__ dbg) {
-  edge_body<T>(blockIdx.x * blockDim.x + threadIdx.x, Ef, V, sten, nrm, w5, w3, Ua, h, ph, err, dbg);
+                                              uint8_t* __restrict__ dbg, const float* __restrict__ wref) {
+  edge_body<T>(blockIdx.x * blockDim.x + threadIdx.x, Ef, V, sten, nrm, w5, w3, Ua, h, ph, err, dbg,
+               wref);
 }
 
 // ------------------------------------------------------------------ k_div
@@ -1238,12 +1413,15 @@ __global__ void __launch_bounds__(128) k_stage(KernelArgs ka, StageArgs sa, Phys
       ghost_body(g, ka.G, ka.V, ka.gid, ka.gdonor, ka.gflags, U, sa.Un, ka.err);
     if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
   }
+  __shared__ float s0f[4];
+  __shared__ double s0d[4];
+  if constexpr (std::is_same<T, float>::value) block_reference(sa.Us, ka.V, s0f, s0d);
   for (int v = tid; v < ka.V; v += stride)
-    vertex_body<T, VISC>(v, ka.V, sa.Us, (T*)ka.Ua, (T*)ka.FG, (T*)ka.FGv, ph);
+    vertex_body<T, VISC>(v, ka.V, sa.Us, (T*)ka.Ua, (T*)ka.FG, (T*)ka.FGv, ph, ka.wref, s0f, s0d);
   if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
   for (int e = tid; e < ka.Ef; e += stride)
     edge_body<T>(e, ka.Ef, ka.V, ka.sten, (const T*)ka.nrm, (const T*)ka.w5, (const T*)ka.w3,
-                 (const T*)ka.Ua, (T*)ka.h, ph, ka.err);
+                 (const T*)ka.Ua, (T*)ka.h, ph, ka.err, nullptr, ka.wref);
   if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
   // every lane of a warp runs the same number of iterations (shuffles inside div_body)
   const long long total = (long long)ka.A * G;
@@ -1264,7 +1442,7 @@ KernelArgs kernel_args(const DevMesh& m) {
   a.gid = m.gid; a.gdonor = m.gdonor; a.gflags = m.gflags; a.vmem = m.vmem;
   a.nrm = m.nrm; a.w5 = m.w5; a.w3 = m.w3; a.cv = m.cv; a.ce = m.ce; a.cvis = m.cvis;
   a.Ua = m.Ua; a.FG = m.FG; a.FGv = m.FGv; a.h = m.h;
-  a.dtbits = m.dtbits; a.dt_last = m.dt_last; a.err = m.err; a.bar = m.bar;
+  a.dtbits = m.dtbits; a.dt_last = m.dt_last; a.err = m.err; a.bar = m.bar; a.wref = m.wref;
   a.spins = m.barrier_spins;
   return a;
 }
@@ -1280,14 +1458,17 @@ cudaError_t launch_vertex(const DevMesh& m, const double* U, const Phys& ph, cud
   if (m.precision == 0) {
     if (m.viscous)
       k_vertex<double, true><<<nb, 256, 0, s>>>(m.V, U, (double*)m.Ua, (double*)m.FG,
-                                                (double*)m.FGv, ph);
+                                                (double*)m.FGv, ph, nullptr);
     else
-      k_vertex<double, false><<<nb, 256, 0, s>>>(m.V, U, (double*)m.Ua, (double*)m.FG, nullptr, ph);
+      k_vertex<double, false><<<nb, 256, 0, s>>>(m.V, U, (double*)m.Ua, (double*)m.FG, nullptr, ph,
+                                                 nullptr);
   } else {
     if (m.viscous)
-      k_vertex<float, true><<<nb, 256, 0, s>>>(m.V, U, (float*)m.Ua, (float*)m.FG, (float*)m.FGv, ph);
+      k_vertex<float, true><<<nb, 256, 0, s>>>(m.V, U, (float*)m.Ua, (float*)m.FG, (float*)m.FGv, ph,
+                                               m.wref);
     else
-      k_vertex<float, false><<<nb, 256, 0, s>>>(m.V, U, (float*)m.Ua, (float*)m.FG, nullptr, ph);
+      k_vertex<float, false><<<nb, 256, 0, s>>>(m.V, U, (float*)m.Ua, (float*)m.FG, nullptr, ph,
+                                                m.wref);
   }
   return cudaGetLastError();
 }
@@ -1298,11 +1479,11 @@ cudaError_t launch_edge(const DevMesh& m, const Phys& ph, cudaStream_t s) {
   if (m.precision == 0)
     k_edge<double><<<nb, 128, 0, s>>>(m.Ef, m.V, m.sten, (const double*)m.nrm, (const double*)m.w5,
                                       (const double*)m.w3, (const double*)m.Ua, (double*)m.h, ph,
-                                      m.err, m.dbg_branch);
+                                      m.err, m.dbg_branch, nullptr);
   else
     k_edge<float><<<nb, 128, 0, s>>>(m.Ef, m.V, m.sten, (const float*)m.nrm, (const float*)m.w5,
                                      (const float*)m.w3, (const float*)m.Ua, (float*)m.h, ph, m.err,
-                                     m.dbg_branch);
+                                     m.dbg_branch, m.wref);
   return cudaGetLastError();
 }
 

@@ -94,6 +94,8 @@ struct DevMesh {
   // scratch: AoS copies of the state [V][12], vertex fluxes [V][8] (+ viscous), edge fluxes [Ef][4]
   void* Ua = nullptr;
   void* FG = nullptr;
+  // FP32 bulk: the reference state of the stage's deviations (4 floats, written by k_vertex)
+  float* wref = nullptr;
   // testing aid: when set, k_edge writes per flux edge the Alg. 1 branch it took (bit side*4+q
   // set: the WENO-weighted 3-node value of characteristic component q on side L (0) or R (1))
   uint8_t* dbg_branch = nullptr;
@@ -114,6 +116,7 @@ struct KernelArgs {
   unsigned* err;
   unsigned* bar;
   unsigned spins;
+  float* wref;
 };
 
 // Ghost refresh of U; fixed ghosts (donor -1) take their values from `base` (the step's input

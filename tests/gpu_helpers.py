@@ -158,19 +158,34 @@ def run_checked_build_cases(pkg, torch):
 
 
 def c2_chunk_oracle_residual(task):
-    """Spawned worker: the oracle residual of the n x n four-quadrant mesh (5 ghost layers) at a
-    chunk of active vertices, with the library's own coefficients for that chunk (loaded from the
-    .npz of its preprocessing arrays), and the chunk's vertices that read an edge whose sensor
-    lies within 1e-9 of a threshold.  Returns (chunk, R[:, chunk], near-threshold vertices)."""
+    """Spawned worker: the oracle's residual of the n x n four-quadrant mesh (5 ghost layers)
+    at a chunk of active vertices, on the library's own coefficients for that chunk (loaded
+    from the .npz of its preprocessing arrays), and the chunk's vertices that read an edge
+    whose sensor lies within 1e-9 of a threshold.  The discrete structure -- every needed
+    edge's 6-node stencil (Sec. 2.1) and each vertex's two-level set (R7) -- comes from the
+    oracle's own functions and must equal the library's; the coefficient solves are not
+    repeated (the coefficients are the library's, compared elsewhere).  Returns (chunk,
+    R[:, chunk], near-threshold vertices)."""
+    import scipy.sparse as sp
     import synth
+    from oracle import hfd_oracle as H
     n, chunk, lib_path = task
-    lib = np.load(lib_path)
+    with np.load(lib_path) as z:                # every array read once
+        lib = {k: z[k] for k in z.files}
     m = synth.jittered_box_with_ghosts(n, n, (0.0, 1.0), (0.0, 1.0), 5, seed=2)
     U = synth.four_quadrant(m)
-    P = oracle.prepare(m, active=chunk)
+    topo = oracle.build_topology(m)
+    V, E = topo["V"], len(topo["edges"])
+    sets = [oracle.vertex_stencil(topo, int(v)) for v in chunk]
+    need = np.array(sorted(set(int(e) for _, es in sets for e in es)), dtype=np.int64)
+    P = H.Prep()
+    P.topo, P.active, P.opts, P.edges = topo, np.asarray(chunk, dtype=np.int64), oracle.Options(), need
+    geo = [oracle.edge_geometry(m, topo, int(e)) for e in need]
+    P.stencil = np.array([g[0] for g in geo], dtype=np.int64).reshape(-1, 6)
+    P.normal = np.array([g[3] for g in geo]).reshape(-1, 2)
     fe = lib["flux_edges"]
-    pos = np.searchsorted(fe, P.edges)
-    assert np.array_equal(fe[pos], P.edges)
+    pos = np.searchsorted(fe, need)
+    assert np.array_equal(fe[pos], need)
     assert np.array_equal(lib["stencil"].reshape(-1, 6)[pos], P.stencil)
     P.w5 = lib["w5"].reshape(-1, 2, 15)[pos].copy()
     P.w3 = lib["w3"].reshape(-1, 2, 3, 3)[pos].copy()
@@ -180,17 +195,19 @@ def c2_chunk_oracle_residual(task):
     N = np.diff(lib["div_vptr"])
     M = np.diff(lib["div_eptr"])
     off = np.concatenate([[0], np.cumsum(3 * (2 * N + M))])
-    D = [d.tocsr().copy() for d in P.D]
-    for d in D:
-        d.sort_indices()
-    for i, r in enumerate(rl):
-        L = 2 * N[r] + M[r]
+    cols, vals, ptr = [], [[], [], []], [0]
+    for (verts, edges), r in zip(sets, rl):
+        assert len(verts) == N[r] and len(edges) == M[r]
+        c = np.concatenate([np.stack([2 * verts, 2 * verts + 1], 1).ravel(), 2 * V + edges])
+        L = len(c)
         blk = lib["div_coef"][off[r]:off[r] + 3 * L]
-        for k, d in enumerate(D):
-            a, b = d.indptr[i], d.indptr[i + 1]
-            assert b - a == L
-            d.data[a:b] = blk[k * L:(k + 1) * L]
-    P.D = D
+        cols.append(c)
+        for k in range(3):
+            vals[k].append(blk[k * L:(k + 1) * L])
+        ptr.append(ptr[-1] + L)
+    cols = np.concatenate(cols)
+    P.D = [sp.csr_matrix((np.concatenate(vals[k]), cols, np.array(ptr)), shape=(len(chunk), 2 * V + E))
+           for k in range(3)]
     R = oracle.residual(m, P, U.copy())
     bad = near_threshold_vertices(m, P, U, P.opts)
     return chunk, R[:, chunk], bad
