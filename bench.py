@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-div", default="plain", choices=["plain", "folded"],
+                    help="arithmetic of the FP64 divergence (hfd_mesh_set_fp64_div)")
     ap.add_argument("--fp32-div", default="unstaged", choices=["unstaged", "staged"],
                     help="divergence kernel of the FP32-bulk path (hfd_mesh_set_div_staged)")
     ap.add_argument("--no-variants", action="store_true",
@@ -298,6 +300,8 @@ def run_native(args):
         dm = prep.upload(prec)
         if prec == "fp32" and args.fp32_div == "staged":
             dm.set_div_staged(1)
+        if prec == "fp64" and args.fp64_div == "folded":
+            dm.set_fp64_div(1)
         st = dm.stats_dict()
         Ui = dm.import_state(U_dev)
         # Every timed step advances the initial state of the workload: the method as read here
@@ -358,6 +362,40 @@ def run_native(args):
         X.copy_(Ui)
         dm.step(X, 0.0)
         results[prec]["one_step"] = dm.export_state(X)[0:4].cpu().numpy()
+        # the FP64 divergence in its folded double-float form (hfd_mesh_set_fp64_div), the same
+        # steps from the initial state
+        if prec == "fp64" and not args.no_variants and args.fp64_div == "plain":
+            dm.set_fp64_div(1)
+            for _ in range(args.warmup):
+                X.copy_(Ui)
+                dm.steps(X, 0.0, 1)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                X.copy_(Ui)
+                dm.steps(X, 0.0, 1)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            fv, _, fms = replicas.whole_job_rate(A * 3 * args.steps, ev0.elapsed_time(ev1), dist,
+                                                 device="cuda")
+            fk = {k: 0.0 for k in ("ghost", "vertex", "edge", "div", "dt")}
+            for _ in range(args.steps):
+                X.copy_(Ui)
+                km, _ = dm.steps_profiled(X, 0.0, 1)
+                for k in fk:
+                    fk[k] += km[k]
+            X.copy_(Ui)
+            R_f = dm.residual(X.clone())
+            dm.set_fp64_div(0)
+            R_p = dm.residual(X.clone())
+            rel = float(torch.linalg.norm(R_f - R_p) / torch.linalg.norm(R_p))
+            results[prec]["folded"] = {
+                "value": fv, "ms_per_step": fms / args.steps,
+                "kernel_avg_ms": {k: fk[k] / (3 * args.steps) for k in ("vertex", "edge", "div")},
+                "residual_rel_l2_vs_plain": rel,
+                "form": "FP64 divergence with edge-row endpoint averages folded into the vertex "
+                        "rows, centre-vertex differences in FP64, products in double-float on the "
+                        "FP32 pipe (hfd_mesh_set_fp64_div(1))"}
         # the same steps timed from a developed state: the state after two steps (the method's
         # growth makes later states of this problem inadmissible), with the branch mix of both
         if not args.no_variants:
@@ -464,6 +502,7 @@ def run_native(args):
             "kernels": f32["kernels"]}},
         "state_finite": r["finite"],
         "developed_state": {"fp64": r.get("developed"), "fp32_bulk": f32.get("developed")},
+        "fp64_folded_divergence": r.get("folded"),
         "fma_peaks": fpk,
         "gpu_launches": int(r["launches"]),
         "e2e": r.get("e2e"),

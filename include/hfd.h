@@ -318,6 +318,25 @@ hfd_status hfd_mesh_set_lanes(hfd_mesh* mesh, int32_t lanes);
  * temporary device block; synchronises the stream.  Errors: HFD_ERR_ARG, HFD_ERR_CUDA. */
 hfd_status hfd_edge_branches(hfd_mesh* mesh, double* U, uint8_t* branches, void* stream);
 
+/* Arithmetic of the FP64 divergence (the default is 0).  folded = 1: each least-squares row
+ * (Eq. (flux_polynomials), the d_0, d_x, d_y rows) is evaluated as
+ *   sum_j a'_j (F_j - F_c) + F_c sum_j a'_j + sum_m d_m dh_m,
+ * where F_c is the row's own vertex flux, a' the vertex coefficients with each edge row's
+ * endpoint average (1/2) d_m (F_a + F_b) . n_m folded in (at upload), and dh_m the edge flux
+ * minus that average (written by the edge kernel).  The rows annihilate constant fluxes, so the
+ * remaining terms are small, and the products run in double-float (pairs of FP32 values,
+ * 48-bit significands) on the FP32 pipe; the differences, row sums and final combination stay
+ * FP64.  Accuracy: equal to the plain evaluation within 1e-12 relative on the vortex, the
+ * four-quadrant problem and the circular Sod mesh; on low-Mach flows the energy flux's nearly
+ * divergence-free part still cancels (at Mach 0.1, about 250x), and the 48-bit products leave
+ * ~1e-11 relative there, against ~1e-12 for the plain form.  Speed on the four-quadrant
+ * 1024x1024 mesh (GB300): the divergence 1.55 ms against 2.23 ms, the edge kernel 0.11 ms
+ * slower (it forms dh), the step 11.3 ms against 13.0 ms.  The viscous rows stay FP64.
+ * folded = 0: the plain form, 24 FP64 multiply-adds per stencil vertex and 12 per stencil edge
+ * on the FP64 pipe, with the lane count of hfd_mesh_set_lanes.  Drops captured graphs.
+ * Errors: HFD_ERR_ARG (folded not 0 or 1), HFD_ERR_UNSUPPORTED (folded = 1 on an FP32 mesh). */
+hfd_status hfd_mesh_set_fp64_div(hfd_mesh* mesh, int32_t folded);
+
 /* Divergence kernel of an FP32-bulk mesh (the default is 0).  staged = 1: the staged kernel --
  * a persistent, warp-specialised grid walks tiles of consecutive vertices whose row pointers,
  * index chunks and coefficient chunks (the contiguous streams of the least-squares rows, Eq.

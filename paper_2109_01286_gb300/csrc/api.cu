@@ -169,6 +169,55 @@ hfd_status upload_streams(hfd_mesh* m, const hfd::Prep& P, const std::vector<int
     }
   }
   m->stats.div_nnz = vptr[A] * 2 + eptr[A];
+  if (std::is_same<T, double>::value && A > 0) {
+    // folded double-float divergence: each edge row's endpoint average (1/2) d (F_a + F_b) . n
+    // moves into the two endpoint vertices' coefficients (both are in the row's two-level set),
+    // every coefficient is split into a (hi, lo) float pair, and each row's vertex coefficients
+    // are summed (the exact centre-vertex term)
+    std::vector<float> cvdf(2 * cv.size()), cedf(2 * ce.size());
+    std::vector<double> sig((size_t)6 * A), fold;
+    auto put = [](float* dst, double x) {
+      const float hi = (float)x;
+      dst[0] = hi;
+      dst[1] = (float)(x - (double)hi);
+    };
+    for (int ri = 0; ri < A; ++ri) {
+      const int N = vptr[ri + 1] - vptr[ri], M = eptr[ri + 1] - eptr[ri];
+      const T* cvb = &cv[(size_t)6 * vptr[ri]];
+      const T* ceb = &ce[(size_t)3 * eptr[ri]];
+      fold.assign(cvb, cvb + (size_t)6 * N);
+      for (int j = 0; j < M; ++j) {
+        const int e = eidx[eptr[ri] + j];
+        const double nx = (double)nrm[e], ny = (double)nrm[(size_t)Ef + e];
+        for (int end = 2; end <= 3; ++end) {
+          const int v = sten[(size_t)end * Ef + e];
+          int pos = -1;
+          for (int k = 0; k < N; ++k)
+            if (vidx[vptr[ri] + k] == v) { pos = k; break; }
+          if (pos < 0) {
+            set_error("divergence row %d: an end vertex of its edge %d is not in its vertex set", ri, e);
+            return HFD_ERR_MESH;
+          }
+          for (int row = 0; row < 3; ++row) {
+            const double d = (double)ceb[(size_t)row * M + j];
+            fold[(size_t)(2 * row) * N + pos] += 0.5 * d * nx;
+            fold[(size_t)(2 * row + 1) * N + pos] += 0.5 * d * ny;
+          }
+        }
+      }
+      for (int k = 0; k < 6; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j < N; ++j) acc += fold[(size_t)k * N + j];
+        sig[(size_t)6 * ri + k] = acc;
+      }
+      for (size_t k = 0; k < (size_t)6 * N; ++k) put(&cvdf[2 * ((size_t)6 * vptr[ri] + k)], fold[k]);
+      for (size_t k = 0; k < (size_t)3 * M; ++k) put(&cedf[2 * ((size_t)3 * eptr[ri] + k)], (double)ceb[k]);
+    }
+    TRY(dev_upload(m, &d.cvdf, cvdf));
+    TRY(dev_upload(m, &d.cedf, cedf));
+    TRY(dev_upload(m, (void**)&d.sig, sig));
+    d.div_df = 0;                     // an option (hfd_mesh_set_fp64_div): see hfd.h
+  }
   if (std::is_same<T, float>::value) {
     // FP32 bulk: entries in chunks of 4 (hfd::kDivChunk), each chunk's rows contiguous
     chunk_rows(A, vptr, vidx, 6, cv, P.opts.viscous ? &cvis : nullptr);
@@ -695,6 +744,20 @@ hfd_status hfd_edge_branches(hfd_mesh* m, double* U, uint8_t* branches, void* st
     }
   }
   for (int fi = 0; fi < Ef; ++fi) branches[m->fperm[fi]] = host[fi];
+  return HFD_OK;
+}
+
+hfd_status hfd_mesh_set_fp64_div(hfd_mesh* m, int32_t folded) {
+  if (!m || (folded != 0 && folded != 1)) {
+    set_error("hfd_mesh_set_fp64_div: folded must be 0 or 1");
+    return HFD_ERR_ARG;
+  }
+  if (folded && !m->dm.cvdf && m->dm.A > 0) {
+    set_error("hfd_mesh_set_fp64_div: the folded double-float divergence exists for FP64 meshes only");
+    return HFD_ERR_UNSUPPORTED;
+  }
+  m->dm.div_df = folded;
+  drop_graphs(m);
   return HFD_OK;
 }
 

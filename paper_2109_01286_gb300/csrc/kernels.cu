@@ -324,6 +324,76 @@ __device__ __forceinline__ void rusanov_flux_dev(const Ref0& r, const float* dl,
   for (int i = 0; i < 4; ++i) hq[i] = 0.5f * (fl[i] + fr[i]) - 0.5f * s * (dr[i] - dl[i]);
 }
 
+// ---- double-float arithmetic for the FP64 divergence in folded form.  GB300 issues FP32 at
+// 64x its FP64 rate, and converts between FP64 and FP32 at the FP64 rate, so the splits below
+// use integer operations only.
+struct F2x {
+  float hi, lo;
+};
+// x as hi + lo: hi = x truncated to 24 significant bits, lo = the remaining 29 bits rounded to
+// 24, so |x - hi - lo| <= 2^-48 |x| for |x| >= 2^-78 (below that lo underflows and only hi is
+// kept).  Zero and values below the float range give 0; infinities and NaN give
+// themselves in hi.
+__device__ __forceinline__ F2x split_df(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int E = (int)((b >> 52) & 0x7ffull);
+  F2x r;
+  r.lo = 0.f;
+  if (E == 0x7ff) {
+    r.hi = __uint_as_float(sign | 0x7f800000u | ((b & 0xfffffffffffffull) ? 0x400000u : 0u));
+    return r;
+  }
+  const int e = E - 1023;
+  if (E == 0 || e < -126) {
+    r.hi = __uint_as_float(sign);
+    return r;
+  }
+  if (e > 127) {
+    r.hi = __uint_as_float(sign | 0x7f800000u);
+    return r;
+  }
+  r.hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffull));
+  const unsigned ml = (unsigned)(b & 0x1fffffffull);          // the low 29 mantissa bits
+  if (ml == 0u) return r;
+  const int top = 31 - __clz((int)ml);                          // 0 .. 28
+  int el = e - 52 + top;
+  unsigned mant;
+  if (top >= 24) {                                              // round to nearest
+    mant = (ml + (1u << (top - 24))) >> (top - 23);
+    if (mant >> 24) { mant >>= 1; ++el; }                       // the rounding carried
+  } else {
+    mant = ml << (23 - top);
+  }
+  if (el < -126) return r;
+  r.lo = __uint_as_float(sign | ((unsigned)(el + 127) << 23) | (mant & 0x7fffffu));
+  return r;
+}
+// A float as the exact double (subnormal floats count as zero).
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned E = (u >> 23) & 0xffu;
+  if (E == 0u) return __longlong_as_double((long long)sign);
+  const unsigned long long eb = E == 0xffu ? 0x7ffull : (unsigned long long)(E - 127u + 1023u);
+  return __longlong_as_double((long long)(sign | (eb << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// (sh, sl) += (ah, al) * (bh, bl): the product's rounding error by FMA and all four partial
+// products, the sum by Knuth's two-sum; the low parts are accumulated without renormalising.  Explicit roundings keep the
+// compiler from contracting the two-sum.
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  e = __fmaf_rn(al, bl, e);
+  const float s = __fadd_rn(sh, p);
+  const float v = __fsub_rn(s, sh);
+  const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, v)), __fsub_rn(p, v));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
 // rho > 0 and p > 0 (R16), without a division: p = (gamma-1)(E - |m|^2/(2 rho)) has the sign
 // of E rho - |m|^2/2 when rho > 0.
 template <typename T>
@@ -476,7 +546,8 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
                                           const T* __restrict__ nrm, const T* __restrict__ w5,
                                           const T* __restrict__ w3, const T* __restrict__ Ua,
                                           T* __restrict__ h, const Phys& ph, unsigned* err,
-                                          uint8_t* __restrict__ dbg, const float* __restrict__ wref) {
+                                          uint8_t* __restrict__ dbg, const float* __restrict__ wref,
+                                          const double* __restrict__ FGd = nullptr) {
   if (e >= Ef) return;
   const T g1 = phys_g1<T>(ph);
   int s[6];
@@ -642,6 +713,21 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
       rusanov_flux(wside[0], wside[1], nx, ny, g1, hq);
     else
       roe_flux(wside[0], wside[1], nx, ny, g1, phys_harten<T>(ph), phys_half_inv_harten<T>(ph), hq);
+    if (FGd) {
+      // folded divergence: the flux minus the average of the end vertices' projected fluxes
+      // (O(h^2) on smooth data), as float pairs
+      double fa[8], fb[8];
+      ld8(FGd + (size_t)s[2] * 8, fa);
+      ld8(FGd + (size_t)s[3] * 8, fb);
+      F2x t[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        t[q] = split_df(hq[q] - 0.5 * ((fa[q] + fb[q]) * nx + (fa[4 + q] + fb[4 + q]) * ny));
+      float4* o = reinterpret_cast<float4*>(h + (size_t)e * 4);
+      o[0] = make_float4(t[0].hi, t[0].lo, t[1].hi, t[1].lo);
+      o[1] = make_float4(t[2].hi, t[2].lo, t[3].hi, t[3].lo);
+      return;
+    }
   }
   st4(h + (size_t)e * 4, hq);
 }
@@ -659,9 +745,10 @@ __global__ void __launch_bounds__(128, EdgeOcc<T>::kMinBlocks) k_edge(int Ef, in
                                               const T* __restrict__ nrm, const T* __restrict__ w5,
                                               const T* __restrict__ w3, const T* __restrict__ Ua,
                                               T* __restrict__ h, Phys ph, unsigned* err,
-                                              uint8_t* __restrict__ dbg, const float* __restrict__ wref) {
+                                              uint8_t* __restrict__ dbg, const float* __restrict__ wref,
+                                              const double* __restrict__ FGd) {
   edge_body<T>(blockIdx.x * blockDim.x + threadIdx.x, Ef, V, sten, nrm, w5, w3, Ua, h, ph, err, dbg,
-               wref);
+               wref, FGd);
 }
 
 // ------------------------------------------------------------------ k_div
@@ -971,6 +1058,152 @@ __global__ void __launch_bounds__(256, DivOcc<T>::kMinBlocks) k_div(int A, int V
                                              double* dt_last, unsigned* err) {
   div_body<T, G, VISC>(blockIdx.x * blockDim.x + threadIdx.x, A, V, Ef, vptr, vidx, eptr, eidx, cv,
                        ce, cvis, FG, FGv, h, sa, vmem, dtbits, cfl, dt_last, err);
+}
+
+// ------------------------------------------------------------------ k_div, folded double-float (FP64)
+constexpr int kDfLanes = 4;
+// The FP64 divergence with its products on the FP32 pipe.  Every least-squares row annihilates
+// constant fluxes, and every edge row sees the same edge data.  At upload, each edge row's
+// endpoint average, (1/2) d_m (F_a + F_b) . n_m, is folded into the two vertices' coefficients
+// (cvdf), and k_edge stores the remainder dh_m = h_m - (F_a + F_b) . n_m / 2, which is O(h^2)
+// on smooth data.  The rows are then
+//   sum_j a'_j (F_j - F_c) + F_c sum_j a'_j + sum_m d_m dh_m,
+// with the centre vertex's flux F_c subtracted exactly in FP64 (one DADD per value) and the
+// row sums sum_j a'_j precomputed in FP64 (sig).  No term cancels against another any more, so
+// double-float products (48-bit significands, FP32 pipe) keep the FP64 result's accuracy.  The
+// viscous rows, when present, stay in FP64.  kDfLanes lanes per vertex, combined in FP64 by the
+// fixed reduce-scatter of the other divergence kernels (one lane in the persistent form).
+template <int G, bool VISC>
+__device__ __forceinline__ void div_body_df(int gt, int A, int V, int Ef,
+                                            const int32_t* __restrict__ vptr,
+                                            const int32_t* __restrict__ vidx,
+                                            const int32_t* __restrict__ eptr,
+                                            const int32_t* __restrict__ eidx,
+                                            const float2* __restrict__ cvdf,
+                                            const float2* __restrict__ cedf,
+                                            const double* __restrict__ sig,
+                                            const double* __restrict__ cvis,
+                                            const double* __restrict__ FG,
+                                            const double* __restrict__ FGv,
+                                            const float* __restrict__ hdf, const StageArgs& sa,
+                                            const int32_t* __restrict__ vmem,
+                                            const unsigned long long* dtbits, double cfl,
+                                            double* dt_last, unsigned* err) {
+  const int r = gt / G, lane = gt % G;
+  const bool live = r < A;
+  double acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+  if (live) {
+    float sh[12], sl[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { sh[k] = 0.f; sl[k] = 0.f; }
+    double fc[8];
+    ld8(FG + (size_t)r * 8, fc);
+    const int n0 = __ldg(vptr + r), N = __ldg(vptr + r + 1) - n0;
+    const float2* c = cvdf + 6 * (size_t)n0;
+    auto vtx = [&](int j, const double* f) {
+      F2x d[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) d[q] = split_df(f[q] - fc[q]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float2 cf = __ldg(c + (size_t)(2 * k) * N + j), cg = __ldg(c + (size_t)(2 * k + 1) * N + j);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          df_fma(sh[4 * k + q], sl[4 * k + q], cf.x, cf.y, d[q].hi, d[q].lo);
+          df_fma(sh[4 * k + q], sl[4 * k + q], cg.x, cg.y, d[4 + q].hi, d[4 + q].lo);
+        }
+      }
+    };
+    // lanes stride over the entries, two per lane per iteration so that both entries' gathers
+    // are in flight before their arithmetic (the per-lane order is that of one at a time)
+    int j = lane;
+    for (; j + G < N; j += 2 * G) {
+      const int u0 = chk_idx(ld_stream(vidx + n0 + j), V, err), u1 = chk_idx(ld_stream(vidx + n0 + j + G), V, err);
+      double f0[8], f1[8];
+      ld8(FG + (size_t)u0 * 8, f0);
+      ld8(FG + (size_t)u1 * 8, f1);
+      vtx(j, f0);
+      vtx(j + G, f1);
+    }
+    if (j < N) {
+      double f0[8];
+      ld8(FG + (size_t)chk_idx(ld_stream(vidx + n0 + j), V, err) * 8, f0);
+      vtx(j, f0);
+    }
+    const int m0 = __ldg(eptr + r), M = __ldg(eptr + r + 1) - m0;
+    const float2* dd = cedf + 3 * (size_t)m0;
+    auto edg = [&](int jj, const float4& h01, const float4& h23) {
+      const float hh[4] = {h01.x, h01.z, h23.x, h23.z}, hl[4] = {h01.y, h01.w, h23.y, h23.w};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float2 dk = __ldg(dd + (size_t)k * M + jj);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) df_fma(sh[4 * k + q], sl[4 * k + q], dk.x, dk.y, hh[q], hl[q]);
+      }
+    };
+    j = lane;
+    for (; j + G < M; j += 2 * G) {
+      const int e0 = chk_idx(ld_stream(eidx + m0 + j), Ef, err), e1 = chk_idx(ld_stream(eidx + m0 + j + G), Ef, err);
+      const float4* p0 = reinterpret_cast<const float4*>(hdf + (size_t)e0 * 8);
+      const float4* p1 = reinterpret_cast<const float4*>(hdf + (size_t)e1 * 8);
+      const float4 a0 = __ldg(p0), a1 = __ldg(p0 + 1), b0 = __ldg(p1), b1 = __ldg(p1 + 1);
+      edg(j, a0, a1);
+      edg(j + G, b0, b1);
+    }
+    if (j < M) {
+      const float4* p0 = reinterpret_cast<const float4*>(hdf + (size_t)chk_idx(ld_stream(eidx + m0 + j), Ef, err) * 8);
+      edg(j, __ldg(p0), __ldg(p0 + 1));
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = f2d_exact(sh[k]) + f2d_exact(sl[k]);
+    if (lane == 0) {          // the centre-vertex term, once per vertex
+      const double* sg = sig + 6 * (size_t)r;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double sF = __ldg(sg + 2 * k), sG = __ldg(sg + 2 * k + 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[4 * k + q] = __fma_rn(fc[4 + q], sG, __fma_rn(fc[q], sF, acc[4 * k + q]));
+      }
+    }
+    if (VISC) {
+      const double* cz = cvis + 6 * (size_t)n0;
+      for (int jv = lane; jv < N; jv += G) {
+        const int u = chk_idx(ld_stream(vidx + n0 + jv), V, err);
+        double fv[8];
+        ld8(FGv + (size_t)u * 8, fv);
+        const double c0f = ld_stream(cz + jv), c0g = ld_stream(cz + N + jv), cxf = ld_stream(cz + 2 * N + jv);
+        const double cxg = ld_stream(cz + 3 * N + jv), cyf = ld_stream(cz + 4 * N + jv), cyg = ld_stream(cz + 5 * N + jv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[q] = fma(-c0g, fv[4 + q], fma(-c0f, fv[q], acc[q]));
+          acc[4 + q] = fma(-cxg, fv[4 + q], fma(-cxf, fv[q], acc[4 + q]));
+          acc[8 + q] = fma(-cyg, fv[4 + q], fma(-cyf, fv[q], acc[8 + q]));
+        }
+      }
+    }
+  }
+  div_finish<double, G>(r, lane, live, acc, V, sa, vmem, dtbits, cfl, dt_last, err);
+}
+
+template <int G, bool VISC>
+__global__ void __launch_bounds__(256, 2) k_div_df(int A, int V, int Ef, const int32_t* __restrict__ vptr,
+                                                   const int32_t* __restrict__ vidx,
+                                                   const int32_t* __restrict__ eptr,
+                                                   const int32_t* __restrict__ eidx,
+                                                   const float2* __restrict__ cvdf,
+                                                   const float2* __restrict__ cedf,
+                                                   const double* __restrict__ sig,
+                                                   const double* __restrict__ cvis,
+                                                   const double* __restrict__ FG,
+                                                   const double* __restrict__ FGv,
+                                                   const float* __restrict__ hdf, StageArgs sa,
+                                                   const int32_t* __restrict__ vmem,
+                                                   const unsigned long long* dtbits, double cfl,
+                                                   double* dt_last, unsigned* err) {
+  div_body_df<G, VISC>(blockIdx.x * blockDim.x + threadIdx.x, A, V, Ef, vptr, vidx, eptr, eidx, cvdf,
+                    cedf, sig, cvis, FG, FGv, hdf, sa, vmem, dtbits, cfl, dt_last, err);
 }
 
 // ------------------------------------------------------------------ k_div_staged (FP32 bulk)
@@ -1419,10 +1652,22 @@ __global__ void __launch_bounds__(128) k_stage(KernelArgs ka, StageArgs sa, Phys
   for (int v = tid; v < ka.V; v += stride)
     vertex_body<T, VISC>(v, ka.V, sa.Us, (T*)ka.Ua, (T*)ka.FG, (T*)ka.FGv, ph, ka.wref, s0f, s0d);
   if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
+  const double* FGd = nullptr;
+  if constexpr (std::is_same<T, double>::value) FGd = ka.div_df ? (const double*)ka.FG : nullptr;
   for (int e = tid; e < ka.Ef; e += stride)
     edge_body<T>(e, ka.Ef, ka.V, ka.sten, (const T*)ka.nrm, (const T*)ka.w5, (const T*)ka.w3,
-                 (const T*)ka.Ua, (T*)ka.h, ph, ka.err, nullptr, ka.wref);
+                 (const T*)ka.Ua, (T*)ka.h, ph, ka.err, nullptr, ka.wref, FGd);
   if (!grid_barrier(ka.bar, nb, ka.err, ka.spins)) return;
+  if constexpr (std::is_same<T, double>::value) {
+    if (ka.div_df) {        // folded double-float divergence, one lane per vertex
+      for (int r = tid; r < ka.A; r += stride)
+        div_body_df<1, VISC>(r, ka.A, ka.V, ka.Ef, ka.vptr, ka.vidx, ka.eptr, ka.eidx,
+                          (const float2*)ka.cvdf, (const float2*)ka.cedf, ka.sig,
+                          (const double*)ka.cvis, (const double*)ka.FG, (const double*)ka.FGv,
+                          (const float*)ka.h, sa, ka.vmem, ka.dtbits, ph.cfl, ka.dt_last, ka.err);
+      return;
+    }
+  }
   // every lane of a warp runs the same number of iterations (shuffles inside div_body)
   const long long total = (long long)ka.A * G;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride)
@@ -1443,6 +1688,7 @@ KernelArgs kernel_args(const DevMesh& m) {
   a.nrm = m.nrm; a.w5 = m.w5; a.w3 = m.w3; a.cv = m.cv; a.ce = m.ce; a.cvis = m.cvis;
   a.Ua = m.Ua; a.FG = m.FG; a.FGv = m.FGv; a.h = m.h;
   a.dtbits = m.dtbits; a.dt_last = m.dt_last; a.err = m.err; a.bar = m.bar; a.wref = m.wref;
+  a.div_df = m.div_df; a.cvdf = m.cvdf; a.cedf = m.cedf; a.sig = m.sig;
   a.spins = m.barrier_spins;
   return a;
 }
@@ -1479,11 +1725,12 @@ cudaError_t launch_edge(const DevMesh& m, const Phys& ph, cudaStream_t s) {
   if (m.precision == 0)
     k_edge<double><<<nb, 128, 0, s>>>(m.Ef, m.V, m.sten, (const double*)m.nrm, (const double*)m.w5,
                                       (const double*)m.w3, (const double*)m.Ua, (double*)m.h, ph,
-                                      m.err, m.dbg_branch, nullptr);
+                                      m.err, m.dbg_branch, nullptr,
+                                      m.div_df ? (const double*)m.FG : nullptr);
   else
     k_edge<float><<<nb, 128, 0, s>>>(m.Ef, m.V, m.sten, (const float*)m.nrm, (const float*)m.w5,
                                      (const float*)m.w3, (const float*)m.Ua, (float*)m.h, ph, m.err,
-                                     m.dbg_branch, m.wref);
+                                     m.dbg_branch, m.wref, nullptr);
   return cudaGetLastError();
 }
 
@@ -1535,7 +1782,22 @@ cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, dou
                        cudaStream_t s, const double* dt_member) {
   if (m.A == 0) return cudaSuccess;
   StageArgs sa{Us, Un, out, mode, a, b, dt_fixed, dt_member};
-  if (m.precision == 0) {
+  if (m.precision == 0 && m.div_df) {
+    constexpr int G = kDfLanes;
+    const int nb = blocks((long long)m.A * G, 256);
+    if (m.viscous)
+      k_div_df<G, true><<<nb, 256, 0, s>>>(m.A, m.V, m.Ef, m.vptr, m.vidx, m.eptr, m.eidx,
+                                        (const float2*)m.cvdf, (const float2*)m.cedf, m.sig,
+                                        (const double*)m.cvis, (const double*)m.FG,
+                                        (const double*)m.FGv, (const float*)m.h, sa, m.vmem,
+                                        m.dtbits, ph.cfl, m.dt_last, m.err);
+    else
+      k_div_df<G, false><<<nb, 256, 0, s>>>(m.A, m.V, m.Ef, m.vptr, m.vidx, m.eptr, m.eidx,
+                                         (const float2*)m.cvdf, (const float2*)m.cedf, m.sig,
+                                         nullptr, (const double*)m.FG, nullptr,
+                                         (const float*)m.h, sa, m.vmem, m.dtbits, ph.cfl,
+                                         m.dt_last, m.err);
+  } else if (m.precision == 0) {
     switch (lanes) {
       case 1: div_dispatch<double, 1>(m, sa, ph, s); break;
       case 2: div_dispatch<double, 2>(m, sa, ph, s); break;

@@ -96,6 +96,15 @@ struct DevMesh {
   void* FG = nullptr;
   // FP32 bulk: the reference state of the stage's deviations (4 floats, written by k_vertex)
   float* wref = nullptr;
+  // FP64 meshes, folded double-float divergence (div_df = 1): the vertex rows with each edge
+  // row's endpoint average folded in, as (hi, lo) float pairs in the cv layout (cvdf), the edge
+  // rows as float pairs in the ce layout (cedf), and per active vertex the 6 row sums of the
+  // folded vertex rows (sig, FP64: d0F d0G dxF dxG dyF dyG); k_edge then writes each edge's
+  // flux minus the average of its end vertices' projected fluxes, as float pairs, into h
+  int div_df = 0;
+  void* cvdf = nullptr;
+  void* cedf = nullptr;
+  double* sig = nullptr;
   // testing aid: when set, k_edge writes per flux edge the Alg. 1 branch it took (bit side*4+q
   // set: the WENO-weighted 3-node value of characteristic component q on side L (0) or R (1))
   uint8_t* dbg_branch = nullptr;
@@ -117,6 +126,9 @@ struct KernelArgs {
   unsigned* bar;
   unsigned spins;
   float* wref;
+  int div_df;
+  const void *cvdf, *cedf;
+  const double* sig;
 };
 
 // Ghost refresh of U; fixed ghosts (donor -1) take their values from `base` (the step's input

@@ -33,7 +33,7 @@ EXPORTED = ["hfd_default_options", "hfd_last_error", "hfd_prep_create", "hfd_pre
             "hfd_prep_concat", "hfd_mesh_set_launch", "hfd_mesh_set_lanes", "hfd_mesh_autotune",
             "hfd_mesh_set_barrier_limit", "hfd_adjoint", "hfd_batch_create", "hfd_batch_destroy",
             "hfd_batch_mesh", "hfd_batch_step", "hfd_measure_fma_peaks",
-            "hfd_mesh_set_div_staged", "hfd_edge_branches"]
+            "hfd_mesh_set_div_staged", "hfd_edge_branches", "hfd_mesh_set_fp64_div"]
 
 
 class HfdError(RuntimeError):
@@ -126,6 +126,7 @@ _lib.hfd_mesh_autotune.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int32)]
 _lib.hfd_mesh_set_barrier_limit.argtypes = [_P, ctypes.c_uint32]
 _lib.hfd_mesh_set_lanes.argtypes = [_P, ctypes.c_int32]
 _lib.hfd_mesh_set_div_staged.argtypes = [_P, ctypes.c_int32]
+_lib.hfd_mesh_set_fp64_div.argtypes = [_P, ctypes.c_int32]
 _lib.hfd_edge_branches.argtypes = [_P, _P, _P, _P]
 _lib.hfd_adjoint.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
 _lib.hfd_step.argtypes = [_P, _P, ctypes.c_double, _P]
@@ -395,6 +396,11 @@ class Mesh:
         _ok(_lib.hfd_edge_branches(self._h, _dptr(U), out.ctypes.data_as(ctypes.c_void_p),
                                    _stream(stream)), "hfd_edge_branches")
         return out
+
+    def set_fp64_div(self, folded):
+        """hfd_mesh_set_fp64_div: the folded double-float FP64 divergence (1) or the plain FP64
+        one (0)."""
+        _ok(_lib.hfd_mesh_set_fp64_div(self._h, int(folded)), "hfd_mesh_set_fp64_div")
 
     def set_div_staged(self, staged):
         """hfd_mesh_set_div_staged: the staged FP32 divergence (1) or the unstaged one (0)."""
