@@ -43,9 +43,11 @@ CPU_PATCH_N = 32                 # bounded oracle sample: 32 x 32 patch of the s
 # valid for the kernel and data-layout sources they were taken on: when either file's hash
 # differs the figures are stale and the line reports traffic as null
 TRAFFIC_SOURCES = ("paper_2109_01286_gb300/csrc/kernels.cu", "paper_2109_01286_gb300/csrc/api.cu")
-TRAFFIC_SHA = "5fd00e612fddc37f"
-DRAM_TRAFFIC_1024 = {"k_div<double>": 3293.8e6, "k_edge<double>": 1094.0e6,
-                     "k_div<float>": 1794.9e6, "k_edge<float>": 583.4e6}
+TRAFFIC_SHA = "1594dd6971558ee1"
+DRAM_TRAFFIC_1024 = {"k_div<double>": 3275.7e6, "k_edge<double>": 1093.1e6,
+                     "k_vertex<double>": 215.6e6, "k_div<float>": 1794.9e6,
+                     "k_edge<float>": 583.4e6, "k_vertex<float>": 141.3e6,
+                     "k_div_df": 2923.4e6}
 
 
 def sources_sha():
@@ -469,6 +471,10 @@ def run_native(args):
             "dram_gbs": dram(f"k_{dom}<double>", kd["avg_ms"])[0],
             "dram_frac": dram(f"k_{dom}<double>", kd["avg_ms"])[1],
             "hbm_peak_source": peak_src}
+    folded = r.get("folded")
+    if folded is not None:
+        folded["div_traffic"] = traffic("k_div_df")
+        folded["div_dram_gbs"] = dram("k_div_df", folded["kernel_avg_ms"]["div"])[0]
     f32 = results["fp32"]
     dom32 = max(f32["kernels"], key=lambda k: f32["kernels"][k]["share"])
     k32 = f32["kernels"][dom32]
@@ -502,7 +508,7 @@ def run_native(args):
             "kernels": f32["kernels"]}},
         "state_finite": r["finite"],
         "developed_state": {"fp64": r.get("developed"), "fp32_bulk": f32.get("developed")},
-        "fp64_folded_divergence": r.get("folded"),
+        "fp64_folded_divergence": folded,
         "fma_peaks": fpk,
         "gpu_launches": int(r["launches"]),
         "e2e": r.get("e2e"),

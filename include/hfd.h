@@ -318,6 +318,18 @@ hfd_status hfd_mesh_set_lanes(hfd_mesh* mesh, int32_t lanes);
  * temporary device block; synchronises the stream.  Errors: HFD_ERR_ARG, HFD_ERR_CUDA. */
 hfd_status hfd_edge_branches(hfd_mesh* mesh, double* U, uint8_t* branches, void* stream);
 
+/* Testing aid: the integer-only FP64/FP32 conversions of the kernels beside the hardware
+ * conversions.  The FP64 kernels round their FP32 sensor inputs, and the FP32 kernels widen
+ * their sums for the FP64 stage update, with integer operations: GB300 converts between FP64
+ * and FP32 at its FP64 rate.  For each of the n doubles x[i] (device array) writes
+ * f_int[i] = x[i] rounded to float by the integer form, f_hw[i] = the hardware's round to
+ * nearest, and, for the float whose bits are the low 32 bits of x[i], d_int[i] = that float
+ * widened by the integer form, d_hw[i] = the hardware widening (device arrays of n, caller
+ * owned).  The two of each pair are equal bit for bit except on NaN (both NaN).  Errors:
+ * HFD_ERR_ARG (n < 0 or a null array with n > 0), HFD_ERR_CUDA. */
+hfd_status hfd_check_conversions(int64_t n, const double* x, float* f_int, float* f_hw,
+                                 double* d_int, double* d_hw, void* stream);
+
 /* Arithmetic of the FP64 divergence (the default is 0).  folded = 1: each least-squares row
  * (Eq. (flux_polynomials), the d_0, d_x, d_y rows) is evaluated as
  *   sum_j a'_j (F_j - F_c) + F_c sum_j a'_j + sum_m d_m dh_m,

@@ -747,6 +747,20 @@ hfd_status hfd_edge_branches(hfd_mesh* m, double* U, uint8_t* branches, void* st
   return HFD_OK;
 }
 
+hfd_status hfd_check_conversions(int64_t n, const double* x, float* f_int, float* f_hw,
+                                 double* d_int, double* d_hw, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !f_int || !f_hw || !d_int || !d_hw))) {
+    set_error("hfd_check_conversions: invalid argument");
+    return HFD_ERR_ARG;
+  }
+  cudaError_t e = hfd::launch_conversions(n, x, f_int, f_hw, d_int, d_hw, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    set_error("hfd_check_conversions: %s", cudaGetErrorString(e));
+    return HFD_ERR_CUDA;
+  }
+  return HFD_OK;
+}
+
 hfd_status hfd_mesh_set_fp64_div(hfd_mesh* m, int32_t folded) {
   if (!m || (folded != 0 && folded != 1)) {
     set_error("hfd_mesh_set_fp64_div: folded must be 0 or 1");

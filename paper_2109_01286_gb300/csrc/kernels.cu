@@ -369,14 +369,45 @@ __device__ __forceinline__ F2x split_df(double x) {
   r.lo = __uint_as_float(sign | ((unsigned)(el + 127) << 23) | (mant & 0x7fffffu));
   return r;
 }
-// A float as the exact double (subnormal floats count as zero).
+// x rounded to the nearest float, ties to even, as the FP64-to-FP32 conversion rounds it, by
+// integer operations only (the FP64 kernels convert their sensor inputs this way, off the FP64
+// pipe).  Finite values and infinities give the conversion's result bit for bit, subnormal
+// floats included; NaN gives a quiet NaN of the same sign.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int E = (int)((b >> 52) & 0x7ffull);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  if (E == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
+  if (E == 0) return __uint_as_float(sign);                // FP64 subnormals round to zero
+  const int e = E - 1023;
+  if (e > 127) return __uint_as_float(sign | 0x7f800000u);
+  // the 53-bit significand loses 29 bits for a normal float, more for a subnormal one
+  const int sh = e >= -126 ? 29 : 29 + (-126 - e);
+  if (sh > 54) return __uint_as_float(sign);               // below half the smallest subnormal
+  const unsigned long long M = m | (1ull << 52);
+  const unsigned long long q = M >> sh, rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  const unsigned qr = (unsigned)q + ((rem > half || (rem == half && (q & 1ull))) ? 1u : 0u);
+  // a normal result: the significand's leading bit adds one to the exponent field (and a
+  // rounding carry to 2^24 adds one more, up to infinity)
+  const unsigned bits = e >= -126 ? ((unsigned)(e + 126) << 23) + qr : qr;
+  return __uint_as_float(sign | bits);
+}
+// A float as the exact double, by integer operations only (as the FP32-to-FP64 conversion
+// gives it, subnormal floats included; NaN stays NaN).
 __device__ __forceinline__ double f2d_exact(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned E = (u >> 23) & 0xffu;
-  if (E == 0u) return __longlong_as_double((long long)sign);
+  const unsigned E = (u >> 23) & 0xffu, mant = u & 0x7fffffu;
+  if (E == 0u) {
+    if (mant == 0u) return __longlong_as_double((long long)sign);
+    // mant * 2^-149 with its leading bit at position t: exponent t - 149, shifted into place
+    const int t = 31 - __clz((int)mant);
+    const unsigned long long m52 = ((unsigned long long)mant << (52 - t)) & 0xfffffffffffffull;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(t + 874) << 52) | m52));
+  }
   const unsigned long long eb = E == 0xffu ? 0x7ffull : (unsigned long long)(E - 127u + 1023u);
-  return __longlong_as_double((long long)(sign | (eb << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+  return __longlong_as_double((long long)(sign | (eb << 52) | ((unsigned long long)mant << 29)));
 }
 // (sh, sl) += (ah, al) * (bh, bl): the product's rounding error by FMA and all four partial
 // products, the sum by Knuth's two-sum; the low parts are accumulated without renormalising.  Explicit roundings keep the
@@ -434,11 +465,11 @@ __device__ __forceinline__ void vertex_body(int v, int V, const double* __restri
     if (v == 0 && wref) st4(wref, w0);
     float d[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) d[r] = (float)(w[r] - s0d[r]);
+    for (int r = 0; r < 4; ++r) d[r] = d2f_rn(w[r] - s0d[r]);
     st4(ua, d);
 #pragma unroll
     for (int i = 1; i < 3; ++i) {
-      float t[4] = {(float)w[4 * i], (float)w[4 * i + 1], (float)w[4 * i + 2], (float)w[4 * i + 3]};
+      float t[4] = {d2f_rn(w[4 * i]), d2f_rn(w[4 * i + 1]), d2f_rn(w[4 * i + 2]), d2f_rn(w[4 * i + 3])};
       st4(ua + 4 * i, t);
     }
     const Ref0 r0 = make_ref(w0, g1);
@@ -525,7 +556,9 @@ __global__ void __launch_bounds__(256) k_vertex(int V, const double* __restrict_
 //    values of that component, form the omega-weighted candidates and back-project.
 constexpr float kGuard = 1e-3f;
 
-__device__ __forceinline__ float sensor_diff(double a, double b) { return (float)(a - b); }
+__device__ __forceinline__ float to_f32(double x) { return d2f_rn(x); }
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float sensor_diff(double a, double b) { return d2f_rn(a - b); }
 __device__ __forceinline__ float sensor_diff(float a, float b) { return a - b; }
 
 template <typename T>
@@ -578,11 +611,12 @@ __device__ __forceinline__ void edge_body(int e, int Ef, int V, const int32_t* _
   // FP32 left eigenvectors at the Roe state of the edge ends (sensor only)
   float Lf[4][4];
   {
-    float fi[4] = {(float)fwi[0], (float)fwi[1], (float)fwi[2], (float)fwi[3]};
-    float fj[4] = {(float)fwj[0], (float)fwj[1], (float)fwj[2], (float)fwj[3]};
+    float fi[4], fj[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { fi[q] = to_f32(fwi[q]); fj[q] = to_f32(fwj[q]); }
     float u, v, H, c;
-    roe_avg(fi, fj, (float)g1, u, v, H, c);
-    left_ev(u, v, c, (float)nx, (float)ny, (float)g1, Lf);
+    roe_avg(fi, fj, ph.g1f, u, v, H, c);
+    left_ev(u, v, c, to_f32(nx), to_f32(ny), ph.g1f, Lf);
   }
   T W5L[4] = {T(0), T(0), T(0), T(0)}, W5R[4] = {T(0), T(0), T(0), T(0)};
   float cf[6][4];
@@ -1901,6 +1935,29 @@ cudaError_t launch_batch_copy(int V, int n, const int64_t* off, double* const* p
 cudaError_t launch_permute(int V, const int32_t* perm, const double* src, double* dst, bool gather,
                            cudaStream_t s) {
   k_permute<<<blocks(V, 256), 256, 0, s>>>(V, perm, src, dst, gather ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// The integer-only conversions against the hardware conversions, element by element: x as a
+// double rounded to float both ways, and the low 32 bits of x as a float widened both ways.
+__global__ void k_conversions(int64_t n, const double* __restrict__ x, float* __restrict__ f_int,
+                              float* __restrict__ f_hw, double* __restrict__ d_int,
+                              double* __restrict__ d_hw) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  f_int[i] = d2f_rn(v);
+  f_hw[i] = __double2float_rn(v);
+  const float f = __uint_as_float((unsigned)(unsigned long long)__double_as_longlong(v));
+  d_int[i] = f2d_exact(f);
+  d_hw[i] = (double)f;
+}
+
+cudaError_t launch_conversions(int64_t n, const double* x, float* f_int, float* f_hw, double* d_int,
+                               double* d_hw, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  k_conversions<<<(unsigned)blocks, 256, 0, s>>>(n, x, f_int, f_hw, d_int, d_hw);
   return cudaGetLastError();
 }
 

@@ -134,6 +134,8 @@ struct KernelArgs {
 // Ghost refresh of U; fixed ghosts (donor -1) take their values from `base` (the step's input
 // state; pass U itself outside a step).
 cudaError_t launch_ghost(const DevMesh& m, double* U, const double* base, cudaStream_t s);
+cudaError_t launch_conversions(int64_t n, const double* x, float* f_int, float* f_hw,
+                               double* d_int, double* d_hw, cudaStream_t s);
 cudaError_t launch_vertex(const DevMesh& m, const double* U, const Phys& ph, cudaStream_t s);
 cudaError_t launch_edge(const DevMesh& m, const Phys& ph, cudaStream_t s);
 // out = R (residual mode) or out = a*Un + b*(Us + dt*R) (stage mode); dt_fixed <= 0 selects

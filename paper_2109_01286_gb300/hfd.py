@@ -33,7 +33,8 @@ EXPORTED = ["hfd_default_options", "hfd_last_error", "hfd_prep_create", "hfd_pre
             "hfd_prep_concat", "hfd_mesh_set_launch", "hfd_mesh_set_lanes", "hfd_mesh_autotune",
             "hfd_mesh_set_barrier_limit", "hfd_adjoint", "hfd_batch_create", "hfd_batch_destroy",
             "hfd_batch_mesh", "hfd_batch_step", "hfd_measure_fma_peaks",
-            "hfd_mesh_set_div_staged", "hfd_edge_branches", "hfd_mesh_set_fp64_div"]
+            "hfd_mesh_set_div_staged", "hfd_edge_branches", "hfd_mesh_set_fp64_div",
+            "hfd_check_conversions"]
 
 
 class HfdError(RuntimeError):
@@ -128,6 +129,7 @@ _lib.hfd_mesh_set_lanes.argtypes = [_P, ctypes.c_int32]
 _lib.hfd_mesh_set_div_staged.argtypes = [_P, ctypes.c_int32]
 _lib.hfd_mesh_set_fp64_div.argtypes = [_P, ctypes.c_int32]
 _lib.hfd_edge_branches.argtypes = [_P, _P, _P, _P]
+_lib.hfd_check_conversions.argtypes = [ctypes.c_int64, _P, _P, _P, _P, _P, _P]
 _lib.hfd_adjoint.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
 _lib.hfd_step.argtypes = [_P, _P, ctypes.c_double, _P]
 _lib.hfd_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32,
@@ -271,6 +273,25 @@ def measure_fma_peaks(stream=None):
     _ok(_lib.hfd_measure_fma_peaks(ctypes.byref(f64), ctypes.byref(f32), ctypes.byref(sms),
                                    _stream(stream)), "hfd_measure_fma_peaks")
     return {"fp64_flops": f64.value, "fp32_flops": f32.value, "sm_count": sms.value}
+
+
+def check_conversions(x, stream=None):
+    """hfd_check_conversions: for a contiguous float64 CUDA tensor x, the integer-only and the
+    hardware FP64-to-FP32 roundings of x, and FP32-to-FP64 widenings of the floats held in the
+    low 32 bits of x, as (f_int, f_hw, d_int, d_hw) tensors."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64
+            and x.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    n = x.numel()
+    f_int = torch.empty(n, dtype=torch.float32, device=x.device)
+    f_hw = torch.empty_like(f_int)
+    d_int = torch.empty(n, dtype=torch.float64, device=x.device)
+    d_hw = torch.empty_like(d_int)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    _ok(_lib.hfd_check_conversions(n, ptr(x), ptr(f_int), ptr(f_hw), ptr(d_int), ptr(d_hw),
+                                   _stream(stream)), "hfd_check_conversions")
+    return f_int, f_hw, d_int, d_hw
 
 
 def _dptr(t):
