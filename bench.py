@@ -542,7 +542,8 @@ def run_native(args):
         # bounded passes of the batched, adjoint and viscous configurations (after the timed
         # regions of the line's own workload)
         for key, fn in (("batched_subset", lambda: variant_batched(fpk, steps=min(args.steps, 10))),
-                        ("adjoint_cost", variant_adjoint), ("tgv_mixed_precision", variant_tgv)):
+                        ("adjoint_cost", variant_adjoint), ("tgv_mixed_precision", variant_tgv),
+                        ("three_d", lambda: variant_3d(fpk, peak_hbm, steps=min(args.steps, 10)))):
             try:
                 line["variants"][key] = fn()
             except Exception as e:                    # reported, never fatal to the line
@@ -619,6 +620,65 @@ def variant_adjoint(reps=10, horizon=20, every=4):
                         "the initial state)",
             "step_ms": step_ms, "adjoint_ms": adj_ms, "adjoint_over_step": adj_ms / step_ms,
             "rollouts": rolls}
+
+
+def variant_3d(fpk, peak_hbm, n=40, steps=10, warmup=3):
+    """The three-dimensional extension (include/hfd3d.h) on an n^3 periodic Kuhn-split
+    tetrahedral box with the vortex tube along z, FP64: vertex-stage updates per second over
+    `steps` timed steps, each from the initial state (the reset copy is inside the timed
+    region, as in the line's own workload), the per-kernel split, and the divergence kernel's
+    arithmetic against the measured FP64 peak.  Algorithmic work of one k3_div launch: 60 FMA
+    per vertex entry (4 rows x 3 fluxes x 5 components), 20 per edge entry, the stage update;
+    its bytes: 4 + 96 per vertex entry, 4 + 32 per edge entry, state in and out."""
+    import torch
+    from paper_2109_01286_gb300 import hfd3d
+    from synth import three_d as T3
+    m = T3.periodic_tet_box(n, n, n, 10.0, 10.0, 10.0, seed=3)
+    t0 = time.perf_counter()
+    mesh = hfd3d.Mesh3(m)
+    prep_s = time.perf_counter() - t0
+    info = mesh.info()
+    U0 = torch.from_numpy(T3.vortex_tube(m)).cuda()
+    V = info["nv"]
+    # fixed step: CFL 0.3 of the initial state, the shortest edge over the largest |u| + c
+    w = U0[0:5].cpu().numpy()
+    p = 0.4 * (w[4] - 0.5 * (w[1] ** 2 + w[2] ** 2 + w[3] ** 2) / w[0])
+    speed = np.sqrt((w[1] ** 2 + w[2] ** 2 + w[3] ** 2) / w[0] ** 2) + np.sqrt(1.4 * p / w[0])
+    dt = 0.3 * 0.7 * (10.0 / n) / float(speed.max())
+    X = U0.clone()
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        mesh.steps(X.copy_(U0), dt, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        mesh.steps(X.copy_(U0), dt, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    mesh.check()
+    finite = bool(torch.isfinite(X).all())
+    km = {"vertex": 0.0, "edge": 0.0, "div": 0.0}
+    for _ in range(steps):
+        t = mesh.steps_profiled(X.copy_(U0), dt, 1)
+        for k in km:
+            km[k] += t[k] / (3 * steps)
+    nv_t, ne_t = info["div_nv_total"], info["div_ne_total"]
+    flops = 2.0 * (60 * nv_t + 20 * ne_t) + 3.0 * 20 * V
+    nbytes = (4 + 96) * nv_t + (4 + 32) * ne_t + 8 * 4 + 3 * 20 * 8 * V
+    div_s = km["div"] / 1000.0
+    return {"workload": f"3D extension: {n}^3 periodic Kuhn-split tetrahedral box (jitter 0.15), "
+                        "vortex tube along z (beta 5, mean flow (1, 1, 0.5)), FP64, fixed step",
+            "vertices": V, "edges": info["nedges"], "div_entries_per_vertex":
+                [nv_t / V, ne_t / V], "prep_seconds": prep_s,
+            "value": V * 3 / (ms / 1000.0), "unit": "vertex-stage/s", "ms_per_step": ms,
+            "state_finite": finite, "kernel_avg_ms": km,
+            "roofline": {"kernel": "k3_div", "bound": "alu", "achieved": flops / div_s / 1e12,
+                         "peak": fpk["fp64_tflops"], "unit": "TFLOP/s",
+                         "frac": flops / div_s / 1e12 / fpk["fp64_tflops"],
+                         "hbm_gbs": nbytes / div_s / 1e9, "hbm_frac": nbytes / div_s / 1e9 / peak_hbm,
+                         "peak_source": fpk["source"]}}
 
 
 def variant_tgv(steps=(1, 5, 20)):

@@ -1,7 +1,7 @@
 """Builds the in-tree shared libraries `_lib/libhfd.so` (CUDA for sm_103a + host C++) and
 `_lib/libhfd_check.so`, the bounds-checked build of the same library.
 
-The translation units compile in parallel: csrc/prep.cpp (g++), the .cu files (nvcc,
+The translation units compile in parallel: csrc/prep.cpp and csrc/prep3.cpp (g++), the .cu files (nvcc,
 -gencode arch=compute_103a,code=sm_103a), and csrc/kernels.cu once more with -DHFD_CHECK=1
 (every gathered index tested on the device, see chk_idx in kernels.cu); then nvcc links each
 library with the CUDA runtime.  Host code is built with -ffp-contract=off (see csrc/prep.cpp) and without
@@ -30,13 +30,15 @@ def _nvcc():
 
 def _sources():
     return [os.path.join(CSRC, f) for f in ("prep.cpp", "kernels.cu", "api.cu", "noalloc.cu",
-                                            "adjoint.cu", "peaks.cu")]
+                                            "adjoint.cu", "peaks.cu", "prep3.cpp", "kernels3d.cu",
+                                            "api3d.cu")]
 
 
 def _deps():
     return _sources() + [os.path.join(CSRC, f) for f in ("prep.hpp", "kernels.hpp", "mesh.hpp",
-                                                         "adjoint_kernels.cuh")] + \
-        [os.path.join(INCLUDE, "hfd.h"), os.path.abspath(__file__)]
+                                                         "adjoint_kernels.cuh", "linalg.hpp",
+                                                         "mesh3.hpp", "kernels3d.hpp")] + \
+        [os.path.join(INCLUDE, "hfd.h"), os.path.join(INCLUDE, "hfd3d.h"), os.path.abspath(__file__)]
 
 
 def up_to_date():

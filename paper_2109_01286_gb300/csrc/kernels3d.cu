@@ -1,0 +1,387 @@
+// CUDA kernels (sm_103a) of the three-dimensional extension of the Hermite FD residual and
+// SSP-RK3 step, FP64.  Per Runge-Kutta stage:
+//   k3_vertex  one thread per vertex: the vertex-major copy of the 20 unknowns and the analytic
+//              flux vectors F, G, K (Sec. 2.3, vertex fluxes, in 3D);
+//   k3_edge    one thread per edge: Alg. 1 in 3D (Roe average of the edge ends, five-wave
+//              characteristic projection along the edge, uniform WENO5 weights as the sensor,
+//              5-node Hermite value or weighted 3-node value per component and side,
+//              back-projection, positivity fallback) and Roe's flux with Harten's fix;
+//   k3_div     one thread per vertex: the CSR gather of the least-squares divergence rows
+//              d_0, d_x, d_y, d_z over the vertex fluxes and edge fluxes (Eq.
+//              (flux_polynomials) in 3D), fused with the SSP-RK3 stage update.
+// The characteristic projection uses the closed forms of the left and right eigenvectors of
+// the flux Jacobian along n with the frame (n, t1, t2): waves q_n - c, entropy, shear along
+// t1, shear along t2, q_n + c.
+#include <cuda_runtime.h>
+
+#include "kernels3d.hpp"
+
+namespace hfd {
+namespace {
+
+constexpr unsigned kErrNonfinite = 1u, kErrPositivity = 2u, kErrIndex = 4u;
+
+__device__ __forceinline__ bool finite3(double x) { return isfinite(x); }
+
+// The eigen-structure of one Roe state along the frame (n, t1, t2).
+struct Eig {
+  double u[3], H, c, qn, q1, q2, K, b1, b2, ic;
+  double n[3], t1[3], t2[3];
+};
+
+__device__ __forceinline__ void roe_state(const double* wl, const double* wr, double g1, Eig& s) {
+  const double rl = sqrt(wl[0]), rr = sqrt(wr[0]);
+  const double pl = g1 * (wl[4] - 0.5 * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]) / wl[0]);
+  const double pr = g1 * (wr[4] - 0.5 * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]) / wr[0]);
+  const double is = 1.0 / (rl + rr);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s.u[k] = (wl[k + 1] / rl + wr[k + 1] / rr) * is;
+  s.H = ((wl[4] + pl) / rl + (wr[4] + pr) / rr) * is;
+  s.K = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
+  s.c = sqrt(g1 * (s.H - 0.5 * s.K));
+  s.ic = 1.0 / s.c;
+  s.qn = s.u[0] * s.n[0] + s.u[1] * s.n[1] + s.u[2] * s.n[2];
+  s.q1 = s.u[0] * s.t1[0] + s.u[1] * s.t1[1] + s.u[2] * s.t1[2];
+  s.q2 = s.u[0] * s.t2[0] + s.u[1] * s.t2[1] + s.u[2] * s.t2[2];
+  s.b1 = g1 * s.ic * s.ic;
+  s.b2 = 0.5 * s.b1 * s.K;
+}
+
+// c = L a for the five conserved components a.
+__device__ __forceinline__ void to_char(const Eig& s, const double* a, double* c) {
+  const double um = s.u[0] * a[1] + s.u[1] * a[2] + s.u[2] * a[3];
+  const double nm = (s.n[0] * a[1] + s.n[1] * a[2] + s.n[2] * a[3]) * s.ic;
+  const double t1m = s.t1[0] * a[1] + s.t1[1] * a[2] + s.t1[2] * a[3];
+  const double t2m = s.t2[0] * a[1] + s.t2[1] * a[2] + s.t2[2] * a[3];
+  const double qc = s.qn * s.ic;
+  c[0] = 0.5 * ((s.b2 + qc) * a[0] - s.b1 * um - nm + s.b1 * a[4]);
+  c[1] = (1.0 - s.b2) * a[0] + s.b1 * um - s.b1 * a[4];
+  c[2] = t1m - s.q1 * a[0];
+  c[3] = t2m - s.q2 * a[0];
+  c[4] = 0.5 * ((s.b2 - qc) * a[0] - s.b1 * um + nm + s.b1 * a[4]);
+}
+
+// w = R c.
+__device__ __forceinline__ void from_char(const Eig& s, const double* c, double* w) {
+  w[0] = c[0] + c[1] + c[4];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    w[k + 1] = (c[0] + c[1] + c[4]) * s.u[k] + (c[4] - c[0]) * s.c * s.n[k] + c[2] * s.t1[k] +
+               c[3] * s.t2[k];
+  w[4] = (c[0] + c[4]) * s.H + (c[4] - c[0]) * s.c * s.qn + c[1] * (0.5 * s.K) + c[2] * s.q1 +
+         c[3] * s.q2;
+}
+
+// rho > 0 and p > 0 (R16): p has the sign of E rho - |m|^2 / 2 when rho > 0.
+__device__ __forceinline__ bool admissible3(const double* w) {
+  return w[0] > 0.0 && w[4] * w[0] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) > 0.0;
+}
+
+// The nonlinear weights of uniform WENO5 (Jiang-Shu indicators, linear weights 1/16, 10/16,
+// 5/16) of the five values u0..u4.
+__device__ __forceinline__ void weno3(double u0, double u1, double u2, double u3, double u4,
+                                      double eps, double* o) {
+  const double e1 = u0 - 2.0 * u1 + u2, f1 = u0 - 4.0 * u1 + 3.0 * u2;
+  const double e2 = u1 - 2.0 * u2 + u3, f2 = u1 - u3;
+  const double e3 = u2 - 2.0 * u3 + u4, f3 = 3.0 * u2 - 4.0 * u3 + u4;
+  const double b1 = 13.0 / 12.0 * (e1 * e1) + 0.25 * (f1 * f1);
+  const double b2 = 13.0 / 12.0 * (e2 * e2) + 0.25 * (f2 * f2);
+  const double b3 = 13.0 / 12.0 * (e3 * e3) + 0.25 * (f3 * f3);
+  const double s1 = eps + b1, s2 = eps + b2, s3 = eps + b3;
+  const double a1 = (1.0 / 16.0) / (s1 * s1), a2 = (10.0 / 16.0) / (s2 * s2), a3 = (5.0 / 16.0) / (s3 * s3);
+  const double s = a1 + a2 + a3;
+  o[0] = a1 / s;
+  o[1] = a2 / s;
+  o[2] = a3 / s;
+}
+
+__device__ __forceinline__ void normal_flux3(const double* w, const double* n, double g1, double* f) {
+  const double ir = 1.0 / w[0];
+  const double un = (w[1] * n[0] + w[2] * n[1] + w[3] * n[2]) * ir;
+  const double p = g1 * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) * ir);
+  f[0] = w[0] * un;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f[k + 1] = w[k + 1] * un + p * n[k];
+  f[4] = (w[4] + p) * un;
+}
+
+// ------------------------------------------------------------------ k3_vertex
+// Ua: 20 values per vertex (160 B); FGK: F, G, K per vertex at a stride of 16 (128 B).
+__global__ void __launch_bounds__(256) k3_vertex(int V, const double* __restrict__ U,
+                                                 double* __restrict__ Ua, double* __restrict__ FGK,
+                                                 double g1) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  double w[20];
+#pragma unroll
+  for (int r = 0; r < 20; ++r) w[r] = U[(size_t)r * V + v];
+  double2* ua = reinterpret_cast<double2*>(Ua + (size_t)20 * v);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) ua[i] = make_double2(w[2 * i], w[2 * i + 1]);
+  const double ir = 1.0 / w[0];
+  const double u = w[1] * ir, vv = w[2] * ir, ww = w[3] * ir;
+  const double p = g1 * (w[4] - 0.5 * (w[1] * u + w[2] * vv + w[3] * ww));
+  const double f[16] = {w[1], w[1] * u + p, w[2] * u, w[3] * u, (w[4] + p) * u,
+                        w[2], w[1] * vv, w[2] * vv + p, w[3] * vv, (w[4] + p) * vv,
+                        w[3], w[1] * ww, w[2] * ww, w[3] * ww + p, (w[4] + p) * ww, 0.0};
+  double2* o = reinterpret_cast<double2*>(FGK + (size_t)16 * v);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) o[i] = make_double2(f[2 * i], f[2 * i + 1]);
+}
+
+// ------------------------------------------------------------------ k3_edge
+// One thread per edge.  Stencil ids (6 x E), frame (9 x E), w5 (40 x E) and w3 (18 x E) are
+// structure-of-arrays streams; node data are gathered from Ua.  h: 8 doubles per edge (5 used).
+__global__ void __launch_bounds__(128) k3_edge(int E, int V, const int32_t* __restrict__ sten,
+                                               const double* __restrict__ frame,
+                                               const double* __restrict__ w5,
+                                               const double* __restrict__ w3,
+                                               const double* __restrict__ Ua,
+                                               double* __restrict__ h, Phys3 ph,
+                                               unsigned* __restrict__ err) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  int s[6];
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    s[k] = __ldg(sten + (size_t)k * E + e);
+    bad |= (unsigned)s[k] >= (unsigned)V;
+  }
+  if (bad) {
+    atomicOr(err, kErrIndex);
+    return;
+  }
+  const double g1 = ph.g1;
+  Eig st;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    st.n[k] = __ldg(frame + (size_t)k * E + e);
+    st.t1[k] = __ldg(frame + (size_t)(3 + k) * E + e);
+    st.t2[k] = __ldg(frame + (size_t)(6 + k) * E + e);
+  }
+  double wi[5], wj[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    wi[q] = __ldg(Ua + (size_t)20 * s[2] + q);
+    wj[q] = __ldg(Ua + (size_t)20 * s[3] + q);
+  }
+  roe_state(wi, wj, g1, st);
+  // characteristic values of the six nodes' values, and the 5-node sums of both sides in
+  // conservative variables
+  double cv[6][5];
+  double W[2][5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) W[0][q] = W[1][q] = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double a[20];
+    const double2* src = reinterpret_cast<const double2*>(Ua + (size_t)20 * s[k]);
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+      const double2 t = __ldg(src + i);
+      a[2 * i] = t.x;
+      a[2 * i + 1] = t.y;
+    }
+    to_char(st, a, cv[k]);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int j = k - side;                 // node index within this side's five
+      if (j < 0 || j > 4) continue;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        const double wt = __ldg(w5 + (size_t)(20 * side + 4 * j + d) * E + e);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) W[side][q] = fma(wt, a[5 * d + q], W[side][q]);
+      }
+    }
+  }
+  // sensor per side and characteristic component; weighted 3-node values where it is rough
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    double o[5][3];
+    unsigned rough = 0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      if (side == 0) weno3(cv[0][q], cv[1][q], cv[2][q], cv[3][q], cv[4][q], ph.eps, o[q]);
+      else           weno3(cv[5][q], cv[4][q], cv[3][q], cv[2][q], cv[1][q], ph.eps, o[q]);
+      const bool smooth = o[q][0] > ph.sens_lo && o[q][0] < ph.sens_hi;
+      if (ph.force_branch == 2 || (ph.force_branch == 0 && !smooth)) rough |= 1u << q;
+    }
+    if (rough) {
+      double C[5];
+      to_char(st, W[side], C);
+      const double* w = w3 + (size_t)(9 * side) * E + e;
+      double wt[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) wt[i] = __ldg(w + (size_t)i * E);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        if (!((rough >> q) & 1u)) continue;
+        double c3[3];
+        if (side == 0) {
+          c3[0] = wt[0] * cv[0][q] + wt[1] * cv[1][q] + wt[2] * cv[2][q];
+          c3[1] = wt[3] * cv[1][q] + wt[4] * cv[2][q] + wt[5] * cv[3][q];
+          c3[2] = wt[6] * cv[2][q] + wt[7] * cv[3][q] + wt[8] * cv[4][q];
+        } else {
+          c3[0] = wt[0] * cv[5][q] + wt[1] * cv[4][q] + wt[2] * cv[3][q];
+          c3[1] = wt[3] * cv[4][q] + wt[4] * cv[3][q] + wt[5] * cv[2][q];
+          c3[2] = wt[6] * cv[3][q] + wt[7] * cv[2][q] + wt[8] * cv[1][q];
+        }
+        C[q] = o[q][0] * c3[0] + o[q][1] * c3[1] + o[q][2] * c3[2];
+      }
+      from_char(st, C, W[side]);
+    }
+  }
+  // positivity (R16): fall back to the end state of that side
+  if (!admissible3(W[0]))
+#pragma unroll
+    for (int q = 0; q < 5; ++q) W[0][q] = wi[q];
+  if (!admissible3(W[1]))
+#pragma unroll
+    for (int q = 0; q < 5; ++q) W[1][q] = wj[q];
+  // Roe's flux along n with Harten's fix on all five waves
+  Eig r;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r.n[k] = st.n[k];
+    r.t1[k] = st.t1[k];
+    r.t2[k] = st.t2[k];
+  }
+  roe_state(W[0], W[1], g1, r);
+  double dw[5], al[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) dw[q] = W[1][q] - W[0][q];
+  to_char(r, dw, al);
+  const double lam[5] = {r.qn - r.c, r.qn, r.qn, r.qn, r.qn + r.c};
+  const double del = ph.harten * r.c, i2del = ph.half_inv_harten * r.ic;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    double a = fabs(lam[i]);
+    if (a < del) a = (lam[i] * lam[i] + del * del) * i2del;
+    al[i] *= a;
+  }
+  double diss[5], fl[5], fr[5];
+  from_char(r, al, diss);
+  normal_flux3(W[0], r.n, g1, fl);
+  normal_flux3(W[1], r.n, g1, fr);
+  double* o = h + (size_t)8 * e;
+  double hq[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) hq[q] = 0.5 * (fl[q] + fr[q]) - 0.5 * diss[q];
+  reinterpret_cast<double2*>(o)[0] = make_double2(hq[0], hq[1]);
+  reinterpret_cast<double2*>(o)[1] = make_double2(hq[2], hq[3]);
+  o[4] = hq[4];
+}
+
+// ------------------------------------------------------------------ k3_div
+// One thread per vertex: acc[5 r + q] = sum over the row r (d_0, d_x, d_y, d_z) of the vertex
+// entries (12 coefficients each against F, G, K of the entry's vertex) and the edge entries (4
+// coefficients against h of the entry's edge); R = -acc.  mode 0 writes R; mode 1 writes the
+// stage update b (Us + dt R) + a Un (a = 0: Un is not read) with explicit roundings.
+__global__ void __launch_bounds__(128) k3_div(int V, int E, const int32_t* __restrict__ vptr,
+                                              const int32_t* __restrict__ vidx,
+                                              const double* __restrict__ cv,
+                                              const int32_t* __restrict__ eptr,
+                                              const int32_t* __restrict__ eidx,
+                                              const double* __restrict__ ce,
+                                              const double* __restrict__ FGK,
+                                              const double* __restrict__ h, int mode,
+                                              const double* __restrict__ Us, const double* Un,
+                                              double* out, double a, double b, double dt,
+                                              unsigned* __restrict__ err) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  double acc[20];
+#pragma unroll
+  for (int i = 0; i < 20; ++i) acc[i] = 0.0;
+  unsigned bad = 0;
+  const int j0 = __ldg(vptr + v), j1 = __ldg(vptr + v + 1);
+  for (int j = j0; j < j1; ++j) {
+    const int u = __ldg(vidx + j);
+    if ((unsigned)u >= (unsigned)V) {
+      bad |= kErrIndex;
+      continue;
+    }
+    double c[12], f[16];
+    const double2* cs = reinterpret_cast<const double2*>(cv + (size_t)12 * j);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const double2 t = __ldg(cs + i);
+      c[2 * i] = t.x;
+      c[2 * i + 1] = t.y;
+    }
+    const double2* fs = reinterpret_cast<const double2*>(FGK + (size_t)16 * u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const double2 t = __ldg(fs + i);
+      f[2 * i] = t.x;
+      f[2 * i + 1] = t.y;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+        acc[5 * r + q] = fma(c[3 * r], f[q], fma(c[3 * r + 1], f[5 + q], fma(c[3 * r + 2], f[10 + q], acc[5 * r + q])));
+  }
+  const int k0 = __ldg(eptr + v), k1 = __ldg(eptr + v + 1);
+  for (int j = k0; j < k1; ++j) {
+    const int ed = __ldg(eidx + j);
+    if ((unsigned)ed >= (unsigned)E) {
+      bad |= kErrIndex;
+      continue;
+    }
+    const double2 c01 = __ldg(reinterpret_cast<const double2*>(ce + (size_t)4 * j));
+    const double2 c23 = __ldg(reinterpret_cast<const double2*>(ce + (size_t)4 * j) + 1);
+    const double* hp = h + (size_t)8 * ed;
+    const double2 h01 = __ldg(reinterpret_cast<const double2*>(hp));
+    const double2 h23 = __ldg(reinterpret_cast<const double2*>(hp) + 1);
+    const double hq[5] = {h01.x, h01.y, h23.x, h23.y, __ldg(hp + 4)};
+    const double cr[4] = {c01.x, c01.y, c23.x, c23.y};
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) acc[5 * r + q] = fma(cr[r], hq[q], acc[5 * r + q]);
+  }
+#pragma unroll
+  for (int i = 0; i < 20; ++i) {
+    const double R = -acc[i];
+    const size_t idx = (size_t)i * V + v;
+    double o;
+    if (mode == 0) {
+      o = R;
+    } else {
+      o = __dmul_rn(b, __fma_rn(dt, R, Us[idx]));
+      if (a != 0.0) o = __fma_rn(a, Un[idx], o);
+    }
+    out[idx] = o;
+    if (!finite3(o)) bad |= kErrNonfinite;
+    if (mode == 1 && i == 0 && !(o > 0.0)) bad |= kErrPositivity;
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+}  // namespace
+
+cudaError_t launch3_vertex(const DevMesh3& m, const double* U, const Phys3& ph, cudaStream_t s) {
+  if (m.V == 0) return cudaSuccess;
+  k3_vertex<<<(m.V + 255) / 256, 256, 0, s>>>(m.V, U, m.Ua, m.FGK, ph.g1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch3_edge(const DevMesh3& m, const Phys3& ph, cudaStream_t s) {
+  if (m.E == 0) return cudaSuccess;
+  k3_edge<<<(m.E + 127) / 128, 128, 0, s>>>(m.E, m.V, m.sten, m.frame, m.w5, m.w3, m.Ua, m.h, ph,
+                                            m.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch3_div(const DevMesh3& m, const double* Us, const double* Un, double* out,
+                        int mode, double a, double b, double dt, cudaStream_t s) {
+  if (m.V == 0) return cudaSuccess;
+  k3_div<<<(m.V + 127) / 128, 128, 0, s>>>(m.V, m.E, m.vptr, m.vidx, m.cv, m.eptr, m.eidx, m.ce,
+                                           m.FGK, m.h, mode, Us, Un, out, a, b, dt, m.err);
+  return cudaGetLastError();
+}
+
+}  // namespace hfd

@@ -30,6 +30,37 @@ def test_library_exports_every_declared_entry_point(pkg):
     assert declared == set(pkg.hfd.EXPORTED)
 
 
+def test_library_exports_every_3d_entry_point(pkg):
+    """The three-dimensional extension's header (include/hfd3d.h): every declared entry point
+    is exported and bound."""
+    from paper_2109_01286_gb300 import hfd3d
+    hdr = open(os.path.join(ROOT, "include", "hfd3d.h")).read()
+    declared = set(re.findall(r"\b(hfd3_[a-z0-9_]+)\s*\(", hdr))
+    assert len(declared) >= 10
+    for name in sorted(declared):
+        assert hasattr(pkg.hfd._lib, name), name
+    assert declared == set(hfd3d.EXPORTED)
+
+
+def test_3d_preprocessing_runs_on_the_host_and_matches_the_oracle_structure(pkg):
+    """hfd3_mesh_create's host preprocessing needs no GPU for its structure, but creating a
+    mesh uploads it; on a machine without a GPU the call fails with HFD_ERR_CUDA after the
+    preprocessing, which the binding reports as an error (never a silent fallback)."""
+    from paper_2109_01286_gb300 import hfd3d
+    from synth import three_d as T
+    m = T.periodic_tet_box(6, 6, 6, 1.0, 1.0, 1.0, seed=1)
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except ImportError:
+        has_gpu = False
+    if has_gpu:
+        pytest.skip("covered by the GPU tests")
+    with pytest.raises(pkg.HfdError) as e:
+        hfd3d.Mesh3(m)
+    assert e.value.status == 5
+
+
 def test_bounds_checked_build_exports_the_same_entry_points(pkg):
     """The bounds-checked library (kernels built with -DHFD_CHECK=1) is built beside the normal
     one and exports every entry point of include/hfd.h."""
