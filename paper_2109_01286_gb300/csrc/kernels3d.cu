@@ -23,23 +23,30 @@ constexpr unsigned kErrNonfinite = 1u, kErrPositivity = 2u, kErrIndex = 4u;
 
 __device__ __forceinline__ bool finite3(double x) { return isfinite(x); }
 
-// The eigen-structure of one Roe state along the frame (n, t1, t2).
+// The eigen-structure of one Roe state along the frame (n, t1, t2), and the two states'
+// reciprocal densities and pressures (shared with the normal fluxes).
 struct Eig {
   double u[3], H, c, qn, q1, q2, K, b1, b2, ic;
   double n[3], t1[3], t2[3];
+  double irl, irr, pl, pr;
 };
 
+// One reciprocal square root per state gives sqrt(rho) and 1/rho, one more gives c and 1/c
+// (the CUDA math library's rsqrt); one division forms the Roe weights.
 __device__ __forceinline__ void roe_state(const double* wl, const double* wr, double g1, Eig& s) {
-  const double rl = sqrt(wl[0]), rr = sqrt(wr[0]);
-  const double pl = g1 * (wl[4] - 0.5 * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]) / wl[0]);
-  const double pr = g1 * (wr[4] - 0.5 * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]) / wr[0]);
-  const double is = 1.0 / (rl + rr);
+  const double sl = rsqrt(wl[0]), sr = rsqrt(wr[0]);
+  s.irl = sl * sl;
+  s.irr = sr * sr;
+  s.pl = g1 * (wl[4] - 0.5 * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]) * s.irl);
+  s.pr = g1 * (wr[4] - 0.5 * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]) * s.irr);
+  const double is = 1.0 / (wl[0] * sl + wr[0] * sr);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) s.u[k] = (wl[k + 1] / rl + wr[k + 1] / rr) * is;
-  s.H = ((wl[4] + pl) / rl + (wr[4] + pr) / rr) * is;
+  for (int k = 0; k < 3; ++k) s.u[k] = (wl[k + 1] * sl + wr[k + 1] * sr) * is;
+  s.H = ((wl[4] + s.pl) * sl + (wr[4] + s.pr) * sr) * is;
   s.K = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
-  s.c = sqrt(g1 * (s.H - 0.5 * s.K));
-  s.ic = 1.0 / s.c;
+  const double c2 = g1 * (s.H - 0.5 * s.K);
+  s.ic = rsqrt(c2);
+  s.c = c2 * s.ic;
   s.qn = s.u[0] * s.n[0] + s.u[1] * s.n[1] + s.u[2] * s.n[2];
   s.q1 = s.u[0] * s.t1[0] + s.u[1] * s.t1[1] + s.u[2] * s.t1[2];
   s.q2 = s.u[0] * s.t2[0] + s.u[1] * s.t2[1] + s.u[2] * s.t2[2];
@@ -77,28 +84,31 @@ __device__ __forceinline__ bool admissible3(const double* w) {
   return w[0] > 0.0 && w[4] * w[0] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) > 0.0;
 }
 
-// The nonlinear weights of uniform WENO5 (Jiang-Shu indicators, linear weights 1/16, 10/16,
-// 5/16) of the five values u0..u4.
+// Uniform WENO5 on the five values u0..u4 (Jiang-Shu indicators, linear weights 1/16, 10/16,
+// 5/16) with every weight multiplied by (eps+b1)^2 (eps+b2)^2 (eps+b3)^2, so that the sensor
+// needs no division: t[i] is weight i times that product and S their sum; omega_i = t[i] / S.
 __device__ __forceinline__ void weno3(double u0, double u1, double u2, double u3, double u4,
-                                      double eps, double* o) {
+                                      double eps, double* t, double& S) {
   const double e1 = u0 - 2.0 * u1 + u2, f1 = u0 - 4.0 * u1 + 3.0 * u2;
   const double e2 = u1 - 2.0 * u2 + u3, f2 = u1 - u3;
   const double e3 = u2 - 2.0 * u3 + u4, f3 = 3.0 * u2 - 4.0 * u3 + u4;
   const double b1 = 13.0 / 12.0 * (e1 * e1) + 0.25 * (f1 * f1);
   const double b2 = 13.0 / 12.0 * (e2 * e2) + 0.25 * (f2 * f2);
   const double b3 = 13.0 / 12.0 * (e3 * e3) + 0.25 * (f3 * f3);
-  const double s1 = eps + b1, s2 = eps + b2, s3 = eps + b3;
-  const double a1 = (1.0 / 16.0) / (s1 * s1), a2 = (10.0 / 16.0) / (s2 * s2), a3 = (5.0 / 16.0) / (s3 * s3);
-  const double s = a1 + a2 + a3;
-  o[0] = a1 / s;
-  o[1] = a2 / s;
-  o[2] = a3 / s;
+  double s1 = eps + b1, s2 = eps + b2, s3 = eps + b3;
+  s1 *= s1;
+  s2 *= s2;
+  s3 *= s3;
+  t[0] = (1.0 / 16.0) * (s2 * s3);
+  t[1] = (10.0 / 16.0) * (s1 * s3);
+  t[2] = (5.0 / 16.0) * (s1 * s2);
+  S = t[0] + t[1] + t[2];
 }
 
-__device__ __forceinline__ void normal_flux3(const double* w, const double* n, double g1, double* f) {
-  const double ir = 1.0 / w[0];
+// F_n(w) from the state, its reciprocal density and its pressure.
+__device__ __forceinline__ void normal_flux3(const double* w, double ir, double p, const double* n,
+                                             double* f) {
   const double un = (w[1] * n[0] + w[2] * n[1] + w[3] * n[2]) * ir;
-  const double p = g1 * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) * ir);
   f[0] = w[0] * un;
 #pragma unroll
   for (int k = 0; k < 3; ++k) f[k + 1] = w[k + 1] * un + p * n[k];
@@ -203,10 +213,18 @@ __global__ void __launch_bounds__(128) k3_edge(int E, int V, const int32_t* __re
     unsigned rough = 0;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      if (side == 0) weno3(cv[0][q], cv[1][q], cv[2][q], cv[3][q], cv[4][q], ph.eps, o[q]);
-      else           weno3(cv[5][q], cv[4][q], cv[3][q], cv[2][q], cv[1][q], ph.eps, o[q]);
-      const bool smooth = o[q][0] > ph.sens_lo && o[q][0] < ph.sens_hi;
-      if (ph.force_branch == 2 || (ph.force_branch == 0 && !smooth)) rough |= 1u << q;
+      double S;
+      if (side == 0) weno3(cv[0][q], cv[1][q], cv[2][q], cv[3][q], cv[4][q], ph.eps, o[q], S);
+      else           weno3(cv[5][q], cv[4][q], cv[3][q], cv[2][q], cv[1][q], ph.eps, o[q], S);
+      // sens_lo < omega_1 < sens_hi, without dividing by S > 0
+      const bool smooth = o[q][0] > ph.sens_lo * S && o[q][0] < ph.sens_hi * S;
+      if (ph.force_branch == 2 || (ph.force_branch == 0 && !smooth)) {
+        rough |= 1u << q;
+        const double iS = 1.0 / S;              // the weights themselves, where they are used
+        o[q][0] *= iS;
+        o[q][1] *= iS;
+        o[q][2] *= iS;
+      }
     }
     if (rough) {
       double C[5];
@@ -263,8 +281,8 @@ __global__ void __launch_bounds__(128) k3_edge(int E, int V, const int32_t* __re
   }
   double diss[5], fl[5], fr[5];
   from_char(r, al, diss);
-  normal_flux3(W[0], r.n, g1, fl);
-  normal_flux3(W[1], r.n, g1, fr);
+  normal_flux3(W[0], r.irl, r.pl, r.n, fl);
+  normal_flux3(W[1], r.irr, r.pr, r.n, fr);
   double* o = h + (size_t)8 * e;
   double hq[5];
 #pragma unroll
