@@ -664,6 +664,12 @@ def variant_3d(fpk, peak_hbm, n=40, steps=10, warmup=3):
         t = mesh.steps_profiled(X.copy_(U0), dt, 1)
         for k in km:
             km[k] += t[k] / (3 * steps)
+    # the divergence gather at one lane per vertex, for comparison with the default four
+    mesh.set_lanes(1)
+    k1 = 0.0
+    for _ in range(steps):
+        k1 += mesh.steps_profiled(X.copy_(U0), dt, 1)["div"] / (3 * steps)
+    mesh.set_lanes(4)
     nv_t, ne_t = info["div_nv_total"], info["div_ne_total"]
     flops = 2.0 * (60 * nv_t + 20 * ne_t) + 3.0 * 20 * V
     nbytes = (4 + 96) * nv_t + (4 + 32) * ne_t + 8 * 4 + 3 * 20 * 8 * V
@@ -673,7 +679,7 @@ def variant_3d(fpk, peak_hbm, n=40, steps=10, warmup=3):
             "vertices": V, "edges": info["nedges"], "div_entries_per_vertex":
                 [nv_t / V, ne_t / V], "prep_seconds": prep_s,
             "value": V * 3 / (ms / 1000.0), "unit": "vertex-stage/s", "ms_per_step": ms,
-            "state_finite": finite, "kernel_avg_ms": km,
+            "state_finite": finite, "kernel_avg_ms": km, "div_ms_one_lane": k1,
             "roofline": {"kernel": "k3_div", "bound": "alu", "achieved": flops / div_s / 1e12,
                          "peak": fpk["fp64_tflops"], "unit": "TFLOP/s",
                          "frac": flops / div_s / 1e12 / fpk["fp64_tflops"],

@@ -110,6 +110,12 @@ hfd_status hfd3_steps(hfd3_mesh* mesh, double* U, double dt, int32_t nsteps, voi
 hfd_status hfd3_steps_profiled(hfd3_mesh* mesh, double* U, double dt, int32_t nsteps, double ms[3],
                                void* stream);
 
+/* Lanes (consecutive threads) per vertex in the divergence gather: 1, 2 or 4 (default 4).  The
+ * lanes take the vertex's entries in turn and their sums are combined by a fixed butterfly, so
+ * every count gives deterministic results that agree with the others to rounding.  Errors:
+ * HFD_ERR_ARG (another count or a null mesh). */
+hfd_status hfd3_mesh_set_lanes(hfd3_mesh* mesh, int32_t lanes);
+
 /* Reads and clears the mesh's device error word (synchronises the device): HFD_OK, or the
  * first of HFD_ERR_MESH (a gathered index out of range, which the kernels skip),
  * HFD_ERR_NONFINITE, HFD_ERR_POSITIVITY recorded since the last check. */

@@ -325,6 +325,15 @@ hfd_status hfd3_steps_profiled(hfd3_mesh* m, double* U, double dt, int32_t nstep
   return st;
 }
 
+hfd_status hfd3_mesh_set_lanes(hfd3_mesh* m, int32_t lanes) {
+  if (!m || (lanes != 1 && lanes != 2 && lanes != 4)) {
+    set_error("hfd3_mesh_set_lanes: lanes must be 1, 2 or 4");
+    return HFD_ERR_ARG;
+  }
+  m->d.lanes = lanes;
+  return HFD_OK;
+}
+
 hfd_status hfd3_check(hfd3_mesh* m) {
   if (!m) {
     set_error("hfd3_check: null mesh");

@@ -293,10 +293,15 @@ __global__ void __launch_bounds__(128) k3_edge(int E, int V, const int32_t* __re
 }
 
 // ------------------------------------------------------------------ k3_div
-// One thread per vertex: acc[5 r + q] = sum over the row r (d_0, d_x, d_y, d_z) of the vertex
-// entries (12 coefficients each against F, G, K of the entry's vertex) and the edge entries (4
-// coefficients against h of the entry's edge); R = -acc.  mode 0 writes R; mode 1 writes the
-// stage update b (Us + dt R) + a Un (a = 0: Un is not read) with explicit roundings.
+// G lanes per vertex (G = 1, 2 or 4, consecutive threads): the lanes take the vertex's entries
+// in turn (lane l the entries l, l + G, ...; adjacent lanes read adjacent coefficient blocks),
+// each accumulates acc[5 r + q] over its entries of the row r (d_0, d_x, d_y, d_z): 12
+// coefficients per vertex entry against F, G, K of the entry's vertex and 4 per edge entry
+// against h of the entry's edge.  The lanes' sums are combined by a fixed butterfly, so the
+// result is deterministic.  R = -acc; mode 0 writes R; mode 1 writes the stage update
+// b (Us + dt R) + a Un (a = 0: Un is not read) with explicit roundings; lane l writes the
+// rows l, l + G, ...
+template <int G>
 __global__ void __launch_bounds__(128) k3_div(int V, int E, const int32_t* __restrict__ vptr,
                                               const int32_t* __restrict__ vidx,
                                               const double* __restrict__ cv,
@@ -308,61 +313,72 @@ __global__ void __launch_bounds__(128) k3_div(int V, int E, const int32_t* __res
                                               const double* __restrict__ Us, const double* Un,
                                               double* out, double a, double b, double dt,
                                               unsigned* __restrict__ err) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V) return;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = gt / G, lane = gt % G;
+  // whole groups stay in the warp for the shuffles (V * G threads rounded up to the block)
+  const bool live = v < V;
   double acc[20];
 #pragma unroll
   for (int i = 0; i < 20; ++i) acc[i] = 0.0;
   unsigned bad = 0;
-  const int j0 = __ldg(vptr + v), j1 = __ldg(vptr + v + 1);
-  for (int j = j0; j < j1; ++j) {
-    const int u = __ldg(vidx + j);
-    if ((unsigned)u >= (unsigned)V) {
-      bad |= kErrIndex;
-      continue;
+  if (live) {
+    const int j0 = __ldg(vptr + v), j1 = __ldg(vptr + v + 1);
+    for (int j = j0 + lane; j < j1; j += G) {
+      const int u = __ldg(vidx + j);
+      if ((unsigned)u >= (unsigned)V) {
+        bad |= kErrIndex;
+        continue;
+      }
+      double c[12], f[16];
+      const double2* cs = reinterpret_cast<const double2*>(cv + (size_t)12 * j);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const double2 t = __ldg(cs + i);
+        c[2 * i] = t.x;
+        c[2 * i + 1] = t.y;
+      }
+      const double2* fs = reinterpret_cast<const double2*>(FGK + (size_t)16 * u);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const double2 t = __ldg(fs + i);
+        f[2 * i] = t.x;
+        f[2 * i + 1] = t.y;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+          acc[5 * r + q] = fma(c[3 * r], f[q], fma(c[3 * r + 1], f[5 + q], fma(c[3 * r + 2], f[10 + q], acc[5 * r + q])));
     }
-    double c[12], f[16];
-    const double2* cs = reinterpret_cast<const double2*>(cv + (size_t)12 * j);
+    const int k0 = __ldg(eptr + v), k1 = __ldg(eptr + v + 1);
+    for (int j = k0 + lane; j < k1; j += G) {
+      const int ed = __ldg(eidx + j);
+      if ((unsigned)ed >= (unsigned)E) {
+        bad |= kErrIndex;
+        continue;
+      }
+      const double2 c01 = __ldg(reinterpret_cast<const double2*>(ce + (size_t)4 * j));
+      const double2 c23 = __ldg(reinterpret_cast<const double2*>(ce + (size_t)4 * j) + 1);
+      const double* hp = h + (size_t)8 * ed;
+      const double2 h01 = __ldg(reinterpret_cast<const double2*>(hp));
+      const double2 h23 = __ldg(reinterpret_cast<const double2*>(hp) + 1);
+      const double hq[5] = {h01.x, h01.y, h23.x, h23.y, __ldg(hp + 4)};
+      const double cr[4] = {c01.x, c01.y, c23.x, c23.y};
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      const double2 t = __ldg(cs + i);
-      c[2 * i] = t.x;
-      c[2 * i + 1] = t.y;
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[5 * r + q] = fma(cr[r], hq[q], acc[5 * r + q]);
     }
-    const double2* fs = reinterpret_cast<const double2*>(FGK + (size_t)16 * u);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const double2 t = __ldg(fs + i);
-      f[2 * i] = t.x;
-      f[2 * i + 1] = t.y;
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int q = 0; q < 5; ++q)
-        acc[5 * r + q] = fma(c[3 * r], f[q], fma(c[3 * r + 1], f[5 + q], fma(c[3 * r + 2], f[10 + q], acc[5 * r + q])));
   }
-  const int k0 = __ldg(eptr + v), k1 = __ldg(eptr + v + 1);
-  for (int j = k0; j < k1; ++j) {
-    const int ed = __ldg(eidx + j);
-    if ((unsigned)ed >= (unsigned)E) {
-      bad |= kErrIndex;
-      continue;
-    }
-    const double2 c01 = __ldg(reinterpret_cast<const double2*>(ce + (size_t)4 * j));
-    const double2 c23 = __ldg(reinterpret_cast<const double2*>(ce + (size_t)4 * j) + 1);
-    const double* hp = h + (size_t)8 * ed;
-    const double2 h01 = __ldg(reinterpret_cast<const double2*>(hp));
-    const double2 h23 = __ldg(reinterpret_cast<const double2*>(hp) + 1);
-    const double hq[5] = {h01.x, h01.y, h23.x, h23.y, __ldg(hp + 4)};
-    const double cr[4] = {c01.x, c01.y, c23.x, c23.y};
+  // butterfly over the group: every lane ends with the group's sums, in the same order
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+  for (int off = 1; off < G; off <<= 1)
 #pragma unroll
-      for (int q = 0; q < 5; ++q) acc[5 * r + q] = fma(cr[r], hq[q], acc[5 * r + q]);
-  }
+    for (int i = 0; i < 20; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off, G);
+  if (!live) return;
 #pragma unroll
   for (int i = 0; i < 20; ++i) {
+    if (i % G != lane) continue;
     const double R = -acc[i];
     const size_t idx = (size_t)i * V + v;
     double o;
@@ -397,8 +413,17 @@ cudaError_t launch3_edge(const DevMesh3& m, const Phys3& ph, cudaStream_t s) {
 cudaError_t launch3_div(const DevMesh3& m, const double* Us, const double* Un, double* out,
                         int mode, double a, double b, double dt, cudaStream_t s) {
   if (m.V == 0) return cudaSuccess;
-  k3_div<<<(m.V + 127) / 128, 128, 0, s>>>(m.V, m.E, m.vptr, m.vidx, m.cv, m.eptr, m.eidx, m.ce,
-                                           m.FGK, m.h, mode, Us, Un, out, a, b, dt, m.err);
+  const int64_t threads = (int64_t)m.V * m.lanes;
+  const unsigned blocks = (unsigned)((threads + 127) / 128);
+  if (m.lanes == 4)
+    k3_div<4><<<blocks, 128, 0, s>>>(m.V, m.E, m.vptr, m.vidx, m.cv, m.eptr, m.eidx, m.ce, m.FGK,
+                                     m.h, mode, Us, Un, out, a, b, dt, m.err);
+  else if (m.lanes == 2)
+    k3_div<2><<<blocks, 128, 0, s>>>(m.V, m.E, m.vptr, m.vidx, m.cv, m.eptr, m.eidx, m.ce, m.FGK,
+                                     m.h, mode, Us, Un, out, a, b, dt, m.err);
+  else
+    k3_div<1><<<blocks, 128, 0, s>>>(m.V, m.E, m.vptr, m.vidx, m.cv, m.eptr, m.eidx, m.ce, m.FGK,
+                                     m.h, mode, Us, Un, out, a, b, dt, m.err);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,7 @@ hfd_status build_prep3(const hfd3_mesh_desc* d, const hfd3_options* o, Prep3* P)
 // Device arrays of a 3D mesh.
 struct DevMesh3 {
   int V = 0, E = 0;
+  int lanes = 4;                // threads per vertex in the divergence gather (1, 2, 4)
   int32_t* sten = nullptr;      // 6 x E (SoA)
   double* frame = nullptr;      // 9 x E (SoA)
   double* w5 = nullptr;         // 40 x E (SoA)

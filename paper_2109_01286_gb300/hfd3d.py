@@ -16,7 +16,7 @@ __all__ = ["Mesh3", "Options3", "options3", "HfdError"]
 
 EXPORTED = ["hfd3_default_options", "hfd3_mesh_create", "hfd3_mesh_destroy", "hfd3_mesh_info",
             "hfd3_prep_size", "hfd3_prep_get", "hfd3_prep_set", "hfd3_residual", "hfd3_steps",
-            "hfd3_steps_profiled", "hfd3_check"]
+            "hfd3_steps_profiled", "hfd3_check", "hfd3_mesh_set_lanes"]
 
 
 class Options3(ctypes.Structure):
@@ -50,6 +50,7 @@ _lib.hfd3_steps.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int32, _P]
 _lib.hfd3_steps_profiled.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int32,
                                      ctypes.POINTER(ctypes.c_double), _P]
 _lib.hfd3_check.argtypes = [_P]
+_lib.hfd3_mesh_set_lanes.argtypes = [_P, ctypes.c_int32]
 
 _INT_ARRAYS = {"edges", "sten", "rank", "vptr", "vidx", "eptr", "eidx"}
 
@@ -137,6 +138,9 @@ class Mesh3:
         _ok(_lib.hfd3_steps_profiled(self._h, _dptr(U), float(dt), int(nsteps), ms,
                                      _stream(stream)), "hfd3_steps_profiled")
         return {"vertex": ms[0], "edge": ms[1], "div": ms[2]}
+
+    def set_lanes(self, lanes):
+        _ok(_lib.hfd3_mesh_set_lanes(self._h, int(lanes)), "hfd3_mesh_set_lanes")
 
     def check(self):
         _ok(_lib.hfd3_check(self._h), "hfd3_check")

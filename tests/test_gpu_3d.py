@@ -228,3 +228,27 @@ def test_3d_argument_validation(box):
         mesh.steps(U, 0.0, 1)                                   # dt must be positive
     with pytest.raises(h.HfdError):
         h.Mesh3(dict(m, tet=np.where(m["tet"] == 3, N ** 3 + 5, m["tet"])))
+
+
+def test_3d_divergence_lane_counts_agree(box):
+    """1, 2 and 4 lanes per vertex in the divergence gather give the same residual and steps to
+    rounding (each count deterministic: two runs are bit-identical)."""
+    h = _cuda()
+    m, P = box
+    U = T.vortex_tube(m)
+    mesh = h.Mesh3(m)
+    out = {}
+    for lanes in (1, 2, 4):
+        mesh.set_lanes(lanes)
+        R = _residual(mesh, U)
+        assert np.array_equal(R, _residual(mesh, U))
+        X = torch.from_numpy(U.copy()).cuda()
+        mesh.steps(X, 0.01, 2)
+        torch.cuda.synchronize()
+        mesh.check()
+        out[lanes] = (R, X.cpu().numpy())
+    for lanes in (2, 4):
+        assert max(_groups(out[lanes][0], out[1][0])) < 1e-13
+        assert np.abs(out[lanes][1] - out[1][1]).max() < 1e-13 * np.abs(out[1][1]).max()
+    with pytest.raises(h.HfdError):
+        mesh.set_lanes(3)
