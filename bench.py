@@ -43,11 +43,11 @@ CPU_PATCH_N = 32                 # bounded oracle sample: 32 x 32 patch of the s
 # valid for the kernel and data-layout sources they were taken on: when either file's hash
 # differs the figures are stale and the line reports traffic as null
 TRAFFIC_SOURCES = ("paper_2109_01286_gb300/csrc/kernels.cu", "paper_2109_01286_gb300/csrc/api.cu")
-TRAFFIC_SHA = "1594dd6971558ee1"
-DRAM_TRAFFIC_1024 = {"k_div<double>": 3275.7e6, "k_edge<double>": 1093.1e6,
-                     "k_vertex<double>": 215.6e6, "k_div<float>": 1794.9e6,
-                     "k_edge<float>": 583.4e6, "k_vertex<float>": 141.3e6,
-                     "k_div_df": 2923.4e6}
+TRAFFIC_SHA = "f9031bbe6070362f"
+DRAM_TRAFFIC_1024 = {"k_div<double>": 3269.0e6, "k_edge<double>": 1094.0e6,
+                     "k_vertex<double>": 215.7e6, "k_div<float>": 1795.1e6,
+                     "k_edge<float>": 583.3e6, "k_vertex<float>": 139.2e6,
+                     "k_div_df": 2923.3e6}
 
 
 def sources_sha():
@@ -75,12 +75,14 @@ def parse():
                     help="skip the bounded batched / adjoint / Taylor-Green passes of the default line")
     ap.add_argument("--workload", default="four-quadrant",
                     choices=["four-quadrant", "batched", "adjoint", "tgv", "conservative", "couette",
-                             "circular-sod", "vortex-order"],
+                             "circular-sod", "vortex-order", "three-d"],
                     help="batched: 256 uneven isentropic-vortex meshes advanced together; "
                          "adjoint: gradient of a 200-step vortex run, checked by differences; "
                          "conservative: the four-quadrant line with median-dual value rows; "
                          "circular-sod: Sec. 3.3 on embedded-circle Delaunay meshes; "
-                         "vortex-order: Sec. 3.1 density error at 50-150 segments per side")
+                         "vortex-order: Sec. 3.1 density error at 50-150 segments per side; "
+                         "three-d: the 3D extension on an n^3 tetrahedral box (--n, default 40 "
+                         "for this workload)")
     ap.add_argument("--directions", type=int, default=64)
     ap.add_argument("--batch", type=int, default=256)
     return ap.parse_args()
@@ -1245,6 +1247,19 @@ def run_circular_sod(args):
     print(json.dumps(line), flush=True)
 
 
+def run_three_d(args):
+    """The 3D extension alone (variant_3d at the size --n, 40 when --n is left at the 2D
+    default), as one JSON line."""
+    n = 40 if args.n == 1024 else args.n
+    peak_hbm, _ = load_peaks()
+    r = variant_3d(fma_peaks(), peak_hbm, n=n, steps=args.steps, warmup=args.warmup)
+    line = {"metric": "vertex-stage updates/s", "workload": "three-d", "value": r["value"],
+            "unit": "vertex-stage/s", "ms_per_step": r["ms_per_step"], "steps": args.steps,
+            "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": r["workload"]}, "roofline": r["roofline"], "detail": r}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1261,6 +1276,8 @@ def main():
         run_circular_sod(args)
     elif args.workload == "vortex-order":
         run_vortex_order(args)
+    elif args.workload == "three-d":
+        run_three_d(args)
     else:
         run_native(args)
 
