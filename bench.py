@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-div", default="plain", choices=["plain", "folded"],
                     help="arithmetic of the FP64 divergence (hfd_mesh_set_fp64_div)")
-    ap.add_argument("--fp32-div", default="unstaged", choices=["unstaged", "staged"],
+    ap.add_argument("--fp32-div", default="unstaged", choices=["unstaged", "staged", "gathers"],
                     help="divergence kernel of the FP32-bulk path (hfd_mesh_set_div_staged)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the bounded batched / adjoint / Taylor-Green passes of the default line")
@@ -304,6 +304,8 @@ def run_native(args):
         dm = prep.upload(prec)
         if prec == "fp32" and args.fp32_div == "staged":
             dm.set_div_staged(1)
+        if prec == "fp32" and args.fp32_div == "gathers":
+            dm.set_div_staged(2)
         if prec == "fp64" and args.fp64_div == "folded":
             dm.set_fp64_div(1)
         st = dm.stats_dict()

@@ -357,8 +357,17 @@ hfd_status hfd_mesh_set_fp64_div(hfd_mesh* mesh, int32_t folded);
  * kernel with the lane count of hfd_mesh_set_lanes, which holds more vertices' gathers in
  * flight per SM and measured faster on the four-quadrant 1024x1024 mesh (0.395 ms against
  * 0.560 ms per launch on a GB300); the autotuner times both.  The two agree to rounding (bit
- * for bit at 8 lanes).  Drops captured graphs.  Errors: HFD_ERR_ARG (staged not 0 or 1),
- * HFD_ERR_UNSUPPORTED (staged = 1 on an FP64 mesh). */
+ * for bit at 8 lanes).  staged = 2 (inviscid FP32-bulk meshes): the gather-staged kernel --
+ * each block of 256 threads takes 64 consecutive vertices at 4 lanes each, first copies the
+ * vertex fluxes and edge fluxes that their rows read, each distinct one once, into shared
+ * memory (lists built at upload, with every chunk's indices rewritten as 16-bit positions in
+ * them), then runs the unstaged kernel's chunk loop against shared memory; bit for bit equal to
+ * the unstaged kernel at 4 lanes, and measured slower on the four-quadrant 1024x1024 mesh
+ * (0.433 ms against 0.395 ms per launch: the unstaged kernel's gathers already hit L1/L2, its
+ * limit is the coefficient stream, and the staging pass adds a round of loads and a barrier
+ * before any arithmetic).  Drops captured graphs.  Errors: HFD_ERR_ARG (staged not 0,
+ * 1 or 2), HFD_ERR_UNSUPPORTED (staged = 1 on an FP64 mesh, staged = 2 on an FP64 or viscous
+ * mesh or one whose tile lists would exceed 160 KB of shared memory). */
 hfd_status hfd_mesh_set_div_staged(hfd_mesh* mesh, int32_t staged);
 
 /* Autotuner: times one Runge-Kutta stage on (a copy of) the device state U, internal order,

@@ -247,6 +247,50 @@ hfd_status upload_streams(hfd_mesh* m, const hfd::Prep& P, const std::vector<int
     d.ntiles = (int)tiles.size() / 8;
     d.div_staged = 0;                 // the unstaged kernel measured faster (see hfd.h)
     TRY(dev_upload(m, (void**)&d.tiles, tiles));
+    // the gather-staged divergence (inviscid): per tile of kGsRows rows the sorted distinct
+    // vertex and edge ids its chunks read, and every chunk entry as its position in them
+    d.gs_ntiles = 0;
+    if (!P.opts.viscous && A > 0) {
+      const int R = hfd::kGsRows, C = hfd::kDivChunk;
+      const int nt = (A + R - 1) / R;
+      std::vector<int32_t> tvp(nt + 1, 0), tep(nt + 1, 0), tvl, tel;
+      std::vector<uint16_t> lv(vidx.size()), le(eidx.size());
+      size_t smem_max = 0;
+      bool fits = true;
+      auto localise = [](const std::vector<int32_t>& idx, size_t k0, size_t k1,
+                         std::vector<int32_t>& list, std::vector<uint16_t>& loc) {
+        std::vector<int32_t> u(idx.begin() + k0, idx.begin() + k1);
+        std::sort(u.begin(), u.end());
+        u.erase(std::unique(u.begin(), u.end()), u.end());
+        if (u.size() > 65535) return (size_t)0;
+        for (size_t k = k0; k < k1; ++k)
+          loc[k] = (uint16_t)(std::lower_bound(u.begin(), u.end(), idx[k]) - u.begin());
+        list.insert(list.end(), u.begin(), u.end());
+        return u.size();
+      };
+      for (int t = 0; t < nt && fits; ++t) {
+        const int r0 = t * R, r1 = std::min(A, r0 + R);
+        const size_t nu = localise(vidx, (size_t)C * vptr[r0], (size_t)C * vptr[r1], tvl, lv);
+        const size_t ne = localise(eidx, (size_t)C * eptr[r0], (size_t)C * eptr[r1], tel, le);
+        const size_t bytes = 32 * nu + 16 * ne;
+        fits = (nu > 0 || vptr[r1] == vptr[r0]) && (ne > 0 || eptr[r1] == eptr[r0]) &&
+               bytes <= (size_t)hfd::kGsSmemMax;
+        smem_max = std::max(smem_max, bytes);
+        tvp[t + 1] = (int32_t)tvl.size();
+        tep[t + 1] = (int32_t)tel.size();
+      }
+      if (fits) {
+        TRY(dev_upload(m, (void**)&d.gtv_ptr, tvp));
+        TRY(dev_upload(m, (void**)&d.gte_ptr, tep));
+        TRY(dev_upload(m, (void**)&d.gtv, tvl));
+        TRY(dev_upload(m, (void**)&d.gte, tel));
+        TRY(dev_upload(m, (void**)&d.lvidx, lv));
+        TRY(dev_upload(m, (void**)&d.leidx, le));
+        d.gs_ntiles = nt;
+        d.gs_smem = (int)std::max<size_t>(smem_max, 16);
+        CK(hfd::prepare_div_gs(d.gs_smem));
+      }
+    }
     // the row-pointer copies read whole int4s up to 3 entries past vptr[A] / eptr[A]
     vptr.resize((size_t)A + 5, vptr[A]);
     eptr.resize((size_t)A + 5, eptr[A]);
@@ -705,12 +749,17 @@ hfd_status hfd_mesh_set_lanes(hfd_mesh* m, int32_t lanes) {
 }
 
 hfd_status hfd_mesh_set_div_staged(hfd_mesh* m, int32_t staged) {
-  if (!m || (staged != 0 && staged != 1)) {
-    set_error("hfd_mesh_set_div_staged: staged must be 0 or 1");
+  if (!m || staged < 0 || staged > 2) {
+    set_error("hfd_mesh_set_div_staged: staged must be 0, 1 or 2");
     return HFD_ERR_ARG;
   }
-  if (staged && m->dm.ntiles == 0 && m->dm.A > 0) {
+  if (staged == 1 && m->dm.ntiles == 0 && m->dm.A > 0) {
     set_error("hfd_mesh_set_div_staged: the staged divergence exists for FP32-bulk meshes only");
+    return HFD_ERR_UNSUPPORTED;
+  }
+  if (staged == 2 && m->dm.gs_ntiles == 0 && m->dm.A > 0) {
+    set_error("hfd_mesh_set_div_staged: the gather-staged divergence exists for inviscid "
+              "FP32-bulk meshes only");
     return HFD_ERR_UNSUPPORTED;
   }
   m->dm.div_staged = staged;
@@ -794,6 +843,7 @@ hfd_status hfd_mesh_autotune(hfd_mesh* m, const double* U, void* stream, int32_t
   struct Cand { int persistent, grid, lanes, staged; };
   std::vector<Cand> cands;
   if (d.ntiles > 0) cands.push_back({0, 0, 8, 1});    // FP32 bulk: the staged divergence
+  if (d.gs_ntiles > 0) cands.push_back({0, 0, 4, 2}); // FP32 bulk, inviscid: staged gathers
   for (int lanes : {1, 2, 4, 8}) {
     int per_sm = 0, nsm = 0;
     CK(hfd::persistent_max_blocks(d, lanes, &per_sm, &nsm));

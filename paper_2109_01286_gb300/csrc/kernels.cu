@@ -1071,6 +1071,91 @@ __device__ __forceinline__ void div_body(int gt, int A, int V, int Ef, const int
   div_finish<T, G>(r, lane, live, acc, V, sa, vmem, dtbits, cfl, dt_last, err);
 }
 
+// FP32 divergence with its stencil gathers staged in shared memory (inviscid meshes): block b
+// holds the rows of tile b (kGsRows consecutive rows, kGsLanes lanes each, the row and lane
+// mapping of k_div<float, 4>).  The host lists, per tile, the distinct vertices and flux edges
+// its chunks read (gtv, gte) and rewrites each chunk's indices as 16-bit positions in those
+// lists (lvidx, leidx).  The block first copies the listed vertex fluxes (8 floats) and edge
+// fluxes (4 floats) into shared memory, each once, then every lane runs the chunk loop of
+// div_gather_chunked with the same loads of coefficients and the same multiply-adds in the
+// same order, reading the fluxes from shared memory: the result equals k_div<float, 4> bit for
+// bit.
+__global__ void __launch_bounds__(256, 4) k_div_gs(
+    int A, int V, int Ef, const int32_t* __restrict__ vptr, const ushort4* __restrict__ lvidx,
+    const int32_t* __restrict__ eptr, const ushort4* __restrict__ leidx,
+    const float* __restrict__ cv, const float* __restrict__ ce, const float* __restrict__ FG,
+    const float* __restrict__ h, const int32_t* __restrict__ gtv_ptr,
+    const int32_t* __restrict__ gtv, const int32_t* __restrict__ gte_ptr,
+    const int32_t* __restrict__ gte, StageArgs sa, const int32_t* __restrict__ vmem,
+    const unsigned long long* dtbits, double cfl, double* dt_last, unsigned* err) {
+  extern __shared__ float4 gs_smem[];
+  const int tile = blockIdx.x;
+  const int v0 = __ldg(gtv_ptr + tile), nv = __ldg(gtv_ptr + tile + 1) - v0;
+  const int e0 = __ldg(gte_ptr + tile), ne = __ldg(gte_ptr + tile + 1) - e0;
+  float4* sFG = gs_smem;            // 2 float4 per listed vertex
+  float4* sH = gs_smem + 2 * nv;    // 1 float4 per listed edge
+  for (int i = threadIdx.x; i < 2 * nv; i += blockDim.x) {
+    const int u = chk_idx(__ldg(gtv + v0 + (i >> 1)), V, err);
+    sFG[i] = __ldg(reinterpret_cast<const float4*>(FG + (size_t)u * 8) + (i & 1));
+  }
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+    const int e = chk_idx(__ldg(gte + e0 + i), Ef, err);
+    sH[i] = __ldg(reinterpret_cast<const float4*>(h + (size_t)e * 4));
+  }
+  __syncthreads();
+  constexpr int G = kGsLanes;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = gt / G, lane = gt % G;
+  const bool live = r < A;
+  float acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = 0.f;
+  if (live) {
+    const int c0 = __ldg(vptr + r), nc = __ldg(vptr + r + 1) - c0;
+    const float4* cc = reinterpret_cast<const float4*>(cv) + 6 * (size_t)c0;
+    for (int ch = lane; ch < nc; ch += G) {
+      const ushort4 u = __ldg(lvidx + c0 + ch);
+      float4 k[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) k[i] = __ldg(cc + 6 * ch + i);
+      const unsigned short ui[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const float4 a = sFG[2 * ui[q4]], bq = sFG[2 * ui[q4] + 1];
+        const float f[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+        const float c0f = f4c(k[0], q4), c0g = f4c(k[1], q4), cxf = f4c(k[2], q4);
+        const float cxg = f4c(k[3], q4), cyf = f4c(k[4], q4), cyg = f4c(k[5], q4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[q] = fmaf(c0g, f[4 + q], fmaf(c0f, f[q], acc[q]));
+          acc[4 + q] = fmaf(cxg, f[4 + q], fmaf(cxf, f[q], acc[4 + q]));
+          acc[8 + q] = fmaf(cyg, f[4 + q], fmaf(cyf, f[q], acc[8 + q]));
+        }
+      }
+    }
+    const int m0 = __ldg(eptr + r), mc = __ldg(eptr + r + 1) - m0;
+    const float4* dd = reinterpret_cast<const float4*>(ce) + 3 * (size_t)m0;
+    for (int ch = lane; ch < mc; ch += G) {
+      const ushort4 e = __ldg(leidx + m0 + ch);
+      const float4 d0 = __ldg(dd + 3 * ch), dx = __ldg(dd + 3 * ch + 1), dy = __ldg(dd + 3 * ch + 2);
+      const unsigned short ei[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const float4 t = sH[ei[q4]];
+        const float hv[4] = {t.x, t.y, t.z, t.w};
+        const float a0 = f4c(d0, q4), ax = f4c(dx, q4), ay = f4c(dy, q4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[q] = fmaf(a0, hv[q], acc[q]);
+          acc[4 + q] = fmaf(ax, hv[q], acc[4 + q]);
+          acc[8 + q] = fmaf(ay, hv[q], acc[8 + q]);
+        }
+      }
+    }
+  }
+  div_finish<float, G>(r, lane, live, acc, V, sa, vmem, dtbits, cfl, dt_last, err);
+}
+
 // FP32 data: memory-latency bound, so at least 4 resident blocks of 256 threads per SM; FP64
 // data: FP64-pipe bound, 2 blocks (without a bound the compiler takes ~168 registers and the
 // kernel loses half its warps).
@@ -1811,6 +1896,11 @@ static cudaError_t div_staged_launch(const DevMesh& m, const StageArgs& sa, cons
   return cudaGetLastError();
 }
 
+cudaError_t prepare_div_gs(int smem_bytes) {
+  if (smem_bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_div_gs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+}
+
 cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, double* out, int mode,
                        double a, double b, double dt_fixed, const Phys& ph, int lanes,
                        cudaStream_t s, const double* dt_member) {
@@ -1838,7 +1928,13 @@ cudaError_t launch_div(const DevMesh& m, const double* Us, const double* Un, dou
       case 8: div_dispatch<double, 8>(m, sa, ph, s); break;
       default: div_dispatch<double, 4>(m, sa, ph, s); break;
     }
-  } else if (m.div_staged && m.ntiles > 0) {
+  } else if (m.div_staged == 2 && m.gs_ntiles > 0) {
+    k_div_gs<<<m.gs_ntiles, kGsRows * kGsLanes, m.gs_smem, s>>>(
+        m.A, m.V, m.Ef, m.vptr, reinterpret_cast<const ushort4*>(m.lvidx), m.eptr,
+        reinterpret_cast<const ushort4*>(m.leidx), (const float*)m.cv, (const float*)m.ce,
+        (const float*)m.FG, (const float*)m.h, m.gtv_ptr, m.gtv, m.gte_ptr, m.gte, sa, m.vmem,
+        m.dtbits, ph.cfl, m.dt_last, m.err);
+  } else if (m.div_staged == 1 && m.ntiles > 0) {
     return m.viscous ? div_staged_launch<true>(m, sa, ph, s) : div_staged_launch<false>(m, sa, ph, s);
   } else {
     switch (lanes) {

@@ -44,6 +44,8 @@ constexpr int kDivChunk = 4;
 // Staged FP32 divergence: vertices per tile, stage buffers per block, bytes of one stage buffer
 // (two row-pointer slots of kStagePtrSlot bytes, then per chunk: vertex indices 16 B, vertex
 // coefficients 96 B (+96 B viscous), edge indices 16 B, edge coefficients 48 B).
+constexpr int kGsLanes = 4, kGsRows = 64;     // gather-staged divergence: lanes, rows per block
+constexpr int kGsSmemMax = 160 * 1024;         // a tile needing more is not built (mode 2 refused)
 constexpr int kStageTileVerts = 32;
 constexpr int kStages = 3;
 constexpr int kStageTileBytes = 36 * 1024;
@@ -78,7 +80,14 @@ struct DevMesh {
   // launch_div uses that kernel (1) or the unstaged one with the mesh's lane count (0)
   int32_t* tiles = nullptr;
   int ntiles = 0;
-  int div_staged = 0;
+  int div_staged = 0;          // 0 unstaged, 1 coefficient streams staged by TMA, 2 gathers staged
+  // FP32 bulk, inviscid: the gather-staged divergence (k_div_gs).  Per tile of kGsRows rows the
+  // distinct vertices (gtv) and flux edges (gte) its chunks read, and each chunk's indices as
+  // 16-bit positions in those lists (lvidx, leidx: 4 per chunk); gs_smem is the largest
+  // tile's shared-memory bytes (32 per vertex, 16 per edge); gs_ntiles 0 = not built.
+  uint16_t *lvidx = nullptr, *leidx = nullptr;
+  int32_t *gtv_ptr = nullptr, *gtv = nullptr, *gte_ptr = nullptr, *gte = nullptr;
+  int gs_ntiles = 0, gs_smem = 0;
   // ghosts
   int32_t *gid = nullptr, *gdonor = nullptr, *gflags = nullptr;
   // time step
@@ -134,6 +143,9 @@ struct KernelArgs {
 // Ghost refresh of U; fixed ghosts (donor -1) take their values from `base` (the step's input
 // state; pass U itself outside a step).
 cudaError_t launch_ghost(const DevMesh& m, double* U, const double* base, cudaStream_t s);
+// Raises k_div_gs's dynamic shared-memory limit to smem_bytes when above the default 48 KB
+// (called once per mesh at upload, outside any stream capture).
+cudaError_t prepare_div_gs(int smem_bytes);
 cudaError_t launch_conversions(int64_t n, const double* x, float* f_int, float* f_hw,
                                double* d_int, double* d_hw, cudaStream_t s);
 cudaError_t launch_vertex(const DevMesh& m, const double* U, const Phys& ph, cudaStream_t s);
