@@ -277,10 +277,11 @@ def test_cfl_step_closed_form(box6):
 @pytest.mark.skipif(os.environ.get("HFD_SKIP_SLOW") == "1", reason="slow oracle refinement")
 def test_residual_truncation_error_converges_on_an_exact_solution():
     """A density wave along x carried by a uniform flow: the exact time derivative of every row
-    is -(u . grad) of it.  From 8^3 to 12^3 the error falls at order >= 3 in the value rows
-    (fourth-order interpolation, degree-4 divergence) and >= 1.5 in the derivative rows."""
+    is -(u . grad) of it.  From 6^3 to 8^3 the error falls at order >= 3 in the value rows
+    (fourth-order interpolation, degree-4 divergence; measured 4.2) and >= 1.5 in the derivative
+    rows (measured 3.3-4.0)."""
     errs = []
-    for n in (8, 12):
+    for n in (6, 8):
         m = T.periodic_tet_box(n, n, n, 1.0, 1.0, 1.0, seed=1)
         P = O.prepare(m)
         vel = (0.5, -0.3, 0.4)
@@ -289,6 +290,6 @@ def test_residual_truncation_error_converges_on_an_exact_solution():
         dUdt = (wave(1e-6) - wave(-1e-6)) / 2e-6
         R = O.residual(m, P, U)
         errs.append([np.abs(R[5 * g:5 * g + 5] - dUdt[5 * g:5 * g + 5]).max() for g in range(4)])
-    order = np.log(np.array(errs[0]) / np.array(errs[1])) / np.log(12 / 8)
+    order = np.log(np.array(errs[0]) / np.array(errs[1])) / np.log(8 / 6)
     assert order[0] >= 3.0
     assert order[1:].min() >= 1.5
