@@ -37,7 +37,7 @@ def _sources():
 def _deps():
     return _sources() + [os.path.join(CSRC, f) for f in ("prep.hpp", "kernels.hpp", "mesh.hpp",
                                                          "adjoint_kernels.cuh", "linalg.hpp",
-                                                         "mesh3.hpp", "kernels3d.hpp")] + \
+                                                         "mesh3.hpp", "kernels3d.hpp", "fp_convert.cuh")] + \
         [os.path.join(INCLUDE, "hfd.h"), os.path.join(INCLUDE, "hfd3d.h"), os.path.abspath(__file__)]
 
 

@@ -116,6 +116,9 @@ hfd_status create(const hfd3_mesh_desc* desc, const hfd3_options* o, hfd3_mesh* 
   m->ph.sens_hi = o->sens_hi;
   m->ph.harten = o->harten;
   m->ph.half_inv_harten = 0.5 / o->harten;
+  m->ph.epsf = (float)o->weno_eps;
+  m->ph.sens_lof = (float)o->sens_lo;
+  m->ph.sens_hif = (float)o->sens_hi;
   m->ph.force_branch = o->force_branch;
   return HFD_OK;
 }

@@ -14,6 +14,7 @@
 // t1, shear along t2, q_n + c.
 #include <cuda_runtime.h>
 
+#include "fp_convert.cuh"
 #include "kernels3d.hpp"
 
 namespace hfd {
@@ -79,6 +80,41 @@ __device__ __forceinline__ void from_char(const Eig& s, const double* c, double*
          c[3] * s.q2;
 }
 
+// The FP32 copy of an eigen-structure for the sensor, rounded by integer operations.
+struct EigF {
+  float u[3], n[3], t1[3], t2[3], ic, qn, q1, q2, b1, b2;
+};
+
+__device__ __forceinline__ void to_f32(const Eig& s, EigF& f) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    f.u[k] = d2f_rn(s.u[k]);
+    f.n[k] = d2f_rn(s.n[k]);
+    f.t1[k] = d2f_rn(s.t1[k]);
+    f.t2[k] = d2f_rn(s.t2[k]);
+  }
+  f.ic = d2f_rn(s.ic);
+  f.qn = d2f_rn(s.qn);
+  f.q1 = d2f_rn(s.q1);
+  f.q2 = d2f_rn(s.q2);
+  f.b1 = d2f_rn(s.b1);
+  f.b2 = d2f_rn(s.b2);
+}
+
+// c = L a in FP32 (the formulas of to_char).
+__device__ __forceinline__ void to_char_f(const EigF& s, const float* a, float* c) {
+  const float um = s.u[0] * a[1] + s.u[1] * a[2] + s.u[2] * a[3];
+  const float nm = (s.n[0] * a[1] + s.n[1] * a[2] + s.n[2] * a[3]) * s.ic;
+  const float t1m = s.t1[0] * a[1] + s.t1[1] * a[2] + s.t1[2] * a[3];
+  const float t2m = s.t2[0] * a[1] + s.t2[1] * a[2] + s.t2[2] * a[3];
+  const float qc = s.qn * s.ic;
+  c[0] = 0.5f * ((s.b2 + qc) * a[0] - s.b1 * um - nm + s.b1 * a[4]);
+  c[1] = (1.0f - s.b2) * a[0] + s.b1 * um - s.b1 * a[4];
+  c[2] = t1m - s.q1 * a[0];
+  c[3] = t2m - s.q2 * a[0];
+  c[4] = 0.5f * ((s.b2 - qc) * a[0] - s.b1 * um + nm + s.b1 * a[4]);
+}
+
 // rho > 0 and p > 0 (R16): p has the sign of E rho - |m|^2 / 2 when rho > 0.
 __device__ __forceinline__ bool admissible3(const double* w) {
   return w[0] > 0.0 && w[4] * w[0] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) > 0.0;
@@ -104,6 +140,26 @@ __device__ __forceinline__ void weno3(double u0, double u1, double u2, double u3
   t[2] = (5.0 / 16.0) * (s1 * s2);
   S = t[0] + t[1] + t[2];
 }
+
+// weno3 in FP32, for the sensor's first pass.
+__device__ __forceinline__ void weno3f(float u0, float u1, float u2, float u3, float u4, float eps,
+                                       float& t0, float& S) {
+  const float e1 = u0 - 2.0f * u1 + u2, f1 = u0 - 4.0f * u1 + 3.0f * u2;
+  const float e2 = u1 - 2.0f * u2 + u3, f2 = u1 - u3;
+  const float e3 = u2 - 2.0f * u3 + u4, f3 = 3.0f * u2 - 4.0f * u3 + u4;
+  float s1 = eps + (13.0f / 12.0f * (e1 * e1) + 0.25f * (f1 * f1));
+  float s2 = eps + (13.0f / 12.0f * (e2 * e2) + 0.25f * (f2 * f2));
+  float s3 = eps + (13.0f / 12.0f * (e3 * e3) + 0.25f * (f3 * f3));
+  s1 *= s1;
+  s2 *= s2;
+  s3 *= s3;
+  t0 = 0.0625f * (s2 * s3);
+  S = t0 + 0.625f * (s1 * s3) + 0.3125f * (s1 * s2);
+}
+
+// Relative width of the band around each sensor threshold inside which the FP32 decision is
+// taken again in FP64.
+constexpr float kGuard3 = 1e-3f;
 
 // F_n(w) from the state, its reciprocal density and its pressure.
 __device__ __forceinline__ void normal_flux3(const double* w, double ir, double p, const double* n,
@@ -177,9 +233,12 @@ __global__ void __launch_bounds__(128) k3_edge(int E, int V, const int32_t* __re
     wj[q] = __ldg(Ua + (size_t)20 * s[3] + q);
   }
   roe_state(wi, wj, g1, st);
-  // characteristic values of the six nodes' values, and the 5-node sums of both sides in
-  // conservative variables
-  double cv[6][5];
+  // FP32 sensor: characteristic values of the six nodes' differences from the tail state (the
+  // WENO indicators see differences only), each difference formed in FP64 and rounded once;
+  // and the 5-node sums of both sides in conservative variables, in FP64
+  EigF sf;
+  to_f32(st, sf);
+  float cf[6][5];
   double W[2][5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) W[0][q] = W[1][q] = 0.0;
@@ -193,63 +252,76 @@ __global__ void __launch_bounds__(128) k3_edge(int E, int V, const int32_t* __re
       a[2 * i] = t.x;
       a[2 * i + 1] = t.y;
     }
-    to_char(st, a, cv[k]);
+    float d[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) d[q] = d2f_rn(a[q] - wi[q]);
+    to_char_f(sf, d, cf[k]);
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const int j = k - side;                 // node index within this side's five
       if (j < 0 || j > 4) continue;
 #pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        const double wt = __ldg(w5 + (size_t)(20 * side + 4 * j + d) * E + e);
+      for (int dd = 0; dd < 4; ++dd) {
+        const double wt = __ldg(w5 + (size_t)(20 * side + 4 * j + dd) * E + e);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) W[side][q] = fma(wt, a[5 * d + q], W[side][q]);
+        for (int q = 0; q < 5; ++q) W[side][q] = fma(wt, a[5 * dd + q], W[side][q]);
       }
     }
   }
-  // sensor per side and characteristic component; weighted 3-node values where it is rough
+  // per side and characteristic component: FP32 decision, taken again in FP64 (on the node
+  // values' characteristic values, as the 3-node candidates need) inside the guard band or on a
+  // non-finite FP32 sum; weighted 3-node values where the decision is rough
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
-    double o[5][3];
-    unsigned rough = 0;
+    unsigned flag = 0;                        // rough in FP32, or undecided
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      double S;
-      if (side == 0) weno3(cv[0][q], cv[1][q], cv[2][q], cv[3][q], cv[4][q], ph.eps, o[q], S);
-      else           weno3(cv[5][q], cv[4][q], cv[3][q], cv[2][q], cv[1][q], ph.eps, o[q], S);
-      // sens_lo < omega_1 < sens_hi, without dividing by S > 0
-      const bool smooth = o[q][0] > ph.sens_lo * S && o[q][0] < ph.sens_hi * S;
-      if (ph.force_branch == 2 || (ph.force_branch == 0 && !smooth)) {
-        rough |= 1u << q;
-        const double iS = 1.0 / S;              // the weights themselves, where they are used
-        o[q][0] *= iS;
-        o[q][1] *= iS;
-        o[q][2] *= iS;
+      if (ph.force_branch == 1) break;
+      if (ph.force_branch == 2) {
+        flag |= 1u << q;
+        continue;
       }
+      float t0, S;
+      if (side == 0) weno3f(cf[0][q], cf[1][q], cf[2][q], cf[3][q], cf[4][q], ph.epsf, t0, S);
+      else           weno3f(cf[5][q], cf[4][q], cf[3][q], cf[2][q], cf[1][q], ph.epsf, t0, S);
+      const float mlo = t0 - ph.sens_lof * S, mhi = ph.sens_hif * S - t0;
+      const bool smooth = mlo > 0.f && mhi > 0.f;
+      const bool clear = isfinite(S) && fabsf(mlo) > kGuard3 * S && fabsf(mhi) > kGuard3 * S;
+      if (!smooth || !clear) flag |= 1u << q;
     }
-    if (rough) {
-      double C[5];
-      to_char(st, W[side], C);
-      const double* w = w3 + (size_t)(9 * side) * E + e;
+    if (!flag) continue;
+    double C[5];
+    to_char(st, W[side], C);
+    bool any = false;
+    const double* w = w3 + (size_t)(9 * side) * E + e;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      if (!((flag >> q) & 1u)) continue;
+      double cq[5];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        const int k = side == 0 ? j : 5 - j;
+        double a[5], c[5];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) a[r] = __ldg(Ua + (size_t)20 * s[k] + r);
+        to_char(st, a, c);
+        cq[j] = c[q];
+      }
+      double o[3], S;
+      weno3(cq[0], cq[1], cq[2], cq[3], cq[4], ph.eps, o, S);
+      const bool smooth = o[0] > ph.sens_lo * S && o[0] < ph.sens_hi * S;
+      if (ph.force_branch != 2 && smooth) continue;
+      const double iS = 1.0 / S;
       double wt[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) wt[i] = __ldg(w + (size_t)i * E);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        if (!((rough >> q) & 1u)) continue;
-        double c3[3];
-        if (side == 0) {
-          c3[0] = wt[0] * cv[0][q] + wt[1] * cv[1][q] + wt[2] * cv[2][q];
-          c3[1] = wt[3] * cv[1][q] + wt[4] * cv[2][q] + wt[5] * cv[3][q];
-          c3[2] = wt[6] * cv[2][q] + wt[7] * cv[3][q] + wt[8] * cv[4][q];
-        } else {
-          c3[0] = wt[0] * cv[5][q] + wt[1] * cv[4][q] + wt[2] * cv[3][q];
-          c3[1] = wt[3] * cv[4][q] + wt[4] * cv[3][q] + wt[5] * cv[2][q];
-          c3[2] = wt[6] * cv[3][q] + wt[7] * cv[2][q] + wt[8] * cv[1][q];
-        }
-        C[q] = o[q][0] * c3[0] + o[q][1] * c3[1] + o[q][2] * c3[2];
-      }
-      from_char(st, C, W[side]);
+      const double c1 = wt[0] * cq[0] + wt[1] * cq[1] + wt[2] * cq[2];
+      const double c2 = wt[3] * cq[1] + wt[4] * cq[2] + wt[5] * cq[3];
+      const double c3 = wt[6] * cq[2] + wt[7] * cq[3] + wt[8] * cq[4];
+      C[q] = (o[0] * iS) * c1 + (o[1] * iS) * c2 + (o[2] * iS) * c3;
+      any = true;
     }
+    if (any) from_char(st, C, W[side]);
   }
   // positivity (R16): fall back to the end state of that side
   if (!admissible3(W[0]))

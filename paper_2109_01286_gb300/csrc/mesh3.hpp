@@ -52,6 +52,7 @@ struct DevMesh3 {
 
 struct Phys3 {
   double gamma, g1, eps, sens_lo, sens_hi, harten, half_inv_harten;
+  float epsf, sens_lof, sens_hif;   // the sensor's constants rounded once to FP32 (host)
   int force_branch;
 };
 
