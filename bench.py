@@ -460,7 +460,7 @@ def run_native(args):
         return DRAM_TRAFFIC_1024.get(name) if (args.n == 1024 and fresh) else None
 
     def dram(name, avg_ms):
-        # the survey's % of HBM: measured DRAM bytes per launch over the live launch time
+        # the % of HBM by DRAM bytes: measured bytes per launch over the live launch time
         t = traffic(name)
         return (None, None) if t is None else (t / (avg_ms / 1000.0) / 1e9, t / (avg_ms / 1000.0) / 1e9 / peak_hbm)
     roof = {"kernel": f"k_{dom}<double>", "bound": "alu", "achieved": kd["tflops"],
@@ -881,7 +881,7 @@ def run_adjoint(args):
     # horizon whose differences agree with the adjoint to 1e-5 on every direction is used.
     requested = nsteps
     horizons = [h for h in (200, 100, 50, 40, 30, 20, 10) if h <= requested]
-    survey = []
+    scan = []
     def make_J(ns, ev, rho_t):
         def J(Ui):
             UN = rollout(Ui, mesh, dt, ns, ev)
@@ -910,12 +910,12 @@ def run_adjoint(args):
         U0i.grad = None
         val = Jh(U0i)
         if not bool(torch.isfinite(val)):
-            survey.append({"steps": hz, "finite": False})
+            scan.append({"steps": hz, "finite": False})
             continue
         val.backward()
         rel = fd_check(Jh, U0i.grad.detach(), 4, 11)
         entry = {"steps": hz, "finite": True, "fd_rel_err_max_4dirs": max(rel)}
-        survey.append(entry)
+        scan.append(entry)
         if max(rel) <= 1e-5:
             rel_all = fd_check(Jh, U0i.grad.detach(), args.directions, 5)
             entry["fd_rel_err_max_all_dirs"] = max(rel_all)
@@ -989,7 +989,7 @@ def run_adjoint(args):
                                f"checkpoint every {every}",
                    "objective": "sum_v A_v (rho - rho_exact)^2 at t_final"},
         "J": val.item(), "t_final": T, "steps_requested": requested, "steps_used": nsteps,
-        "checkpoint_every": every, "horizon_survey": survey,
+        "checkpoint_every": every, "horizon_scan": scan,
         "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
         "ms_step": ms_step, "ms_adjoint_step": ms_adj, "adjoint_over_step": ms_adj / ms_step,
         "fd_directions": args.directions, "fd_rel_err_max": max(rel),
