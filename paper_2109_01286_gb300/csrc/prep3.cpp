@@ -10,7 +10,7 @@
 //   * 3-node weights (Eq. (3nodes_intp) with the degree-2 basis in 3D), minimum norm, in
 //     double-double;
 //   * two-level least-squares divergence rows d_0, d_x, d_y, d_z of the three flux vectors
-//     with degree-4 polynomials (Eq. (flux_polynomials)), by Householder QR with column pivoting.
+//     with degree-4 polynomials (Eq. (flux_polynomials)), by Householder QR.
 // Built with -ffp-contract=off, like the 2D preprocessing.
 #include <algorithm>
 #include <chrono>
@@ -261,6 +261,70 @@ static bool edge3(Prep3& P, const hfd3_options& o, int e, char* msg) {
   return true;
 }
 
+// sum a[i] b[i] over i < n with four partial sums (the compiler keeps reductions in order, so
+// the split is what lets it use vector registers)
+static inline double dot4(const double* a, const double* b, int n) {
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  int i = 0;
+  for (; i + 3 < n; i += 4) {
+    s0 += a[i] * b[i];
+    s1 += a[i + 1] * b[i + 1];
+    s2 += a[i + 2] * b[i + 2];
+    s3 += a[i + 3] * b[i + 3];
+  }
+  for (; i < n; ++i) s0 += a[i] * b[i];
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Rows e_t^T A^+ for the target columns t of a full-column-rank A (m x n, column-major) by
+// Householder QR without pivoting: A = Q R, so the row is Q z with R^T z = e_t.  The 3D
+// divergence fit has full column rank on the meshes it accepts, so pivoting buys nothing
+// there and its repeated column norms cost a third of the factorisation.  Returns
+// min |R_kk| / max |R_kk| as the conditioning estimate (0 for a zero column).
+static double ls_rows3(int m, int n, std::vector<double>& A, const int* targets, int ntarg,
+                       double* rows /* ntarg x m */) {
+  std::vector<double> beta(n, 0.0), v0s(n, 0.0);
+  auto col = [&](int j) { return &A[(size_t)j * m]; };
+  double rmin = INFINITY, rmax = 0.0;
+  for (int k = 0; k < n; ++k) {
+    double* c = col(k);
+    const double nx = std::sqrt(dot4(c + k, c + k, m - k));
+    if (nx == 0.0) return 0.0;
+    const double alpha = c[k] >= 0 ? -nx : nx;
+    const double v0 = c[k] - alpha;
+    const double vtv = v0 * v0 + dot4(c + k + 1, c + k + 1, m - k - 1);
+    const double b = 2.0 / vtv;
+    for (int j = k + 1; j < n; ++j) {
+      double* cj = col(j);
+      const double dot = b * (v0 * cj[k] + dot4(c + k + 1, cj + k + 1, m - k - 1));
+      cj[k] -= dot * v0;
+      for (int i = k + 1; i < m; ++i) cj[i] -= dot * c[i];
+    }
+    c[k] = alpha;
+    beta[k] = b;
+    v0s[k] = v0;
+    rmin = std::min(rmin, std::fabs(alpha));
+    rmax = std::max(rmax, std::fabs(alpha));
+  }
+  std::vector<double> z(n), y(m);
+  for (int t = 0; t < ntarg; ++t) {
+    for (int k = 0; k < n; ++k) {             // R^T z = e_t (forward substitution)
+      double acc = (k == targets[t]) ? 1.0 : 0.0;
+      acc -= dot4(&A[(size_t)k * m], z.data(), k);
+      z[k] = acc / A[(size_t)k * m + k];
+    }
+    for (int i = 0; i < m; ++i) y[i] = i < n ? z[i] : 0.0;
+    for (int k = n - 1; k >= 0; --k) {        // y = H_0 ... H_{n-1} [z; 0]
+      const double* c = col(k);
+      const double dot = beta[k] * (v0s[k] * y[k] + dot4(c + k + 1, y.data() + k + 1, m - k - 1));
+      y[k] -= dot * v0s[k];
+      for (int i = k + 1; i < m; ++i) y[i] -= dot * c[i];
+    }
+    std::memcpy(rows + (size_t)t * m, y.data(), sizeof(double) * m);
+  }
+  return rmax > 0 ? rmin / rmax : 0.0;
+}
+
 // Two-level stencil of vertex v (every vertex within graph distance 2, ascending id, and every
 // edge with both ends in that set, ascending index) and its divergence rows: the least-squares
 // fit of the degree-4 Taylor coefficients (a, b, c) of the flux vectors f, g, k about v in
@@ -268,7 +332,7 @@ static bool edge3(Prep3& P, const hfd3_options& o, int e, char* msg) {
 // edge data (f, g, k) . n at the edge midpoints; d_0 = a_x + b_y + c_z, d_x = a_xx + b_xy + c_xz,
 // d_y = a_xy + b_yy + c_yz, d_z = a_xz + b_yz + c_zz (rows of the pseudo-inverse), unscaled.
 // Fills verts, edges and the 12-per-vertex / 4-per-edge coefficients; returns the QR
-// conditioning estimate.
+// conditioning estimate min |R_kk| / max |R_kk|.
 static double div3(const Prep3& P, int v, std::vector<int>& verts, std::vector<int>& eds,
                    std::vector<double>& cvv, std::vector<double>& cee) {
   std::set<int> s;
@@ -331,14 +395,11 @@ static double div3(const Prep3& P, int v, std::vector<int>& verts, std::vector<i
   }
   // the twelve single rows of A^+ that the four divergence rows sum
   static const int tg[12] = {1, 4, 5, 6, 2, 5, 7, 8, 3, 6, 8, 9};   // per flux f: d0, dx, dy, dz
-  int targ[12][2];
+  int targ[12];
   for (int f = 0; f < 3; ++f)
-    for (int r = 0; r < 4; ++r) {
-      targ[4 * f + r][0] = f * K + tg[4 * f + r];
-      targ[4 * f + r][1] = -1;
-    }
+    for (int r = 0; r < 4; ++r) targ[4 * f + r] = f * K + tg[4 * f + r];
   std::vector<double> rows((size_t)12 * m);
-  const double cond = ls_rows(m, n, A, targ, 12, rows.data());
+  const double cond = ls_rows3(m, n, A, targ, 12, rows.data());
   const double sc[4] = {1.0 / ell, 1.0 / (ell * ell), 1.0 / (ell * ell), 1.0 / (ell * ell)};
   cvv.assign((size_t)12 * N, 0.0);
   cee.assign((size_t)4 * M, 0.0);
