@@ -342,8 +342,8 @@ hfd_status hfd_check_conversions(int64_t n, const double* x, float* f_int, float
  * four-quadrant problem and the circular Sod mesh; on low-Mach flows the energy flux's nearly
  * divergence-free part still cancels (at Mach 0.1, about 250x), and the 48-bit products leave
  * ~1e-11 relative there, against ~1e-12 for the plain form.  Speed on the four-quadrant
- * 1024x1024 mesh (GB300): the divergence 1.55 ms against 2.23 ms, the edge kernel 0.11 ms
- * slower (it forms dh), the step 11.3 ms against 13.0 ms.  The viscous rows stay FP64.
+ * 1024x1024 mesh (GB300): the divergence 1.66 ms against 2.23 ms, the edge kernel 0.11 ms
+ * slower (it forms dh), the step 11.05 ms against 12.45 ms.  The viscous rows stay FP64.
  * folded = 0: the plain form, 24 FP64 multiply-adds per stencil vertex and 12 per stencil edge
  * on the FP64 pipe, with the lane count of hfd_mesh_set_lanes.  Drops captured graphs.
  * Errors: HFD_ERR_ARG (folded not 0 or 1), HFD_ERR_UNSUPPORTED (folded = 1 on an FP32 mesh). */
