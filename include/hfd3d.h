@@ -47,15 +47,18 @@ typedef struct {
  * dropping rule; div_cond_min: a divergence stencil whose pivoted-QR estimate |R_nn| / |R_11|
  * falls below it makes hfd3_mesh_create fail with HFD_ERR_SINGULAR; force_branch: 0 sensor,
  * 1 every side 5-node, 2 every side weighted 3-node (testing aid); threads: host preprocessing
- * threads (0 = all hardware threads). */
+ * threads (0 = all hardware threads); host_only: 1 builds the host preprocessing only (no
+ * device memory, no GPU needed: hfd3_prep_get and hfd3_mesh_info work, the device calls
+ * return HFD_ERR_UNSUPPORTED), 0 also uploads it. */
 typedef struct {
   double gamma, weno_eps, sens_lo, sens_hi, harten, sv_rtol, div_cond_min;
   int32_t force_branch;
   int32_t threads;
+  int32_t host_only;
 } hfd3_options;
 
 /* gamma 1.4, weno_eps 1e-2, sens_lo 0.01, sens_hi 0.79, harten 0.1, sv_rtol 1e-13,
- * div_cond_min 1e-12, force_branch 0, threads 0. */
+ * div_cond_min 1e-12, force_branch 0, threads 0, host_only 0. */
 void hfd3_default_options(hfd3_options* opts);
 
 /* Builds the mesh: host preprocessing in FP64 (edges sorted by (tail, head) with tail < head;

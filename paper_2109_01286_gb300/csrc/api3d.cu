@@ -84,6 +84,7 @@ hfd_status create(const hfd3_mesh_desc* desc, const hfd3_options* o, hfd3_mesh* 
   hfd::DevMesh3& d = m->d;
   d.V = P.V;
   d.E = P.E;
+  if (o->host_only) return HFD_OK;           // host preprocessing only: nothing on the device
   const size_t V = P.V, E = P.E;
   TRY3(dalloc(m, (void**)&d.sten, 6 * E * sizeof(int32_t)));
   TRY3(dalloc(m, (void**)&d.frame, 9 * E * sizeof(double)));
@@ -180,6 +181,7 @@ void hfd3_default_options(hfd3_options* o) {
   o->div_cond_min = 1e-12;
   o->force_branch = 0;
   o->threads = 0;
+  o->host_only = 0;
 }
 
 hfd_status hfd3_mesh_create(const hfd3_mesh_desc* desc, const hfd3_options* opts, hfd3_mesh** out) {
@@ -191,7 +193,8 @@ hfd_status hfd3_mesh_create(const hfd3_mesh_desc* desc, const hfd3_options* opts
   hfd3_options o;
   hfd3_default_options(&o);
   if (opts) o = *opts;
-  if (!(o.gamma > 1.0) || !(o.harten > 0.0) || o.force_branch < 0 || o.force_branch > 2) {
+  if (!(o.gamma > 1.0) || !(o.harten > 0.0) || o.force_branch < 0 || o.force_branch > 2 ||
+      (o.host_only != 0 && o.host_only != 1)) {
     set_error("hfd3_mesh_create: invalid options");
     return HFD_ERR_ARG;
   }
@@ -265,6 +268,7 @@ hfd_status hfd3_prep_set(hfd3_mesh* m, const char* name, const void* src, int64_
       }
   }
   std::memcpy(a.p, src, (size_t)a.n * a.elt);
+  if (!m->d.err) return HFD_OK;               // host-only mesh: no device copy to refresh
   const std::string s(name);
   if (s == "cv") return put(m->P.cv, m->d.cv);
   if (s == "ce") return put(m->P.ce, m->d.ce);
@@ -275,6 +279,10 @@ hfd_status hfd3_residual(hfd3_mesh* m, const double* U, double* R, void* stream)
   if (!m || !U || !R || U == R) {
     set_error("hfd3_residual: invalid argument");
     return HFD_ERR_ARG;
+  }
+  if (!m->d.err) {
+    set_error("hfd3_residual: the mesh was built host-only");
+    return HFD_ERR_UNSUPPORTED;
   }
   cudaStream_t s = (cudaStream_t)stream;
   CK3(hfd::launch3_vertex(m->d, U, m->ph, s));
@@ -311,6 +319,10 @@ hfd_status hfd3_steps(hfd3_mesh* m, double* U, double dt, int32_t nsteps, void* 
     set_error("hfd3_steps: invalid argument");
     return HFD_ERR_ARG;
   }
+  if (!m->d.err) {
+    set_error("hfd3_steps: the mesh was built host-only");
+    return HFD_ERR_UNSUPPORTED;
+  }
   return steps_impl(m, U, dt, nsteps, (cudaStream_t)stream, nullptr, nullptr);
 }
 
@@ -319,6 +331,10 @@ hfd_status hfd3_steps_profiled(hfd3_mesh* m, double* U, double dt, int32_t nstep
   if (!m || !U || !ms || !(dt > 0.0) || nsteps < 0) {
     set_error("hfd3_steps_profiled: invalid argument");
     return HFD_ERR_ARG;
+  }
+  if (!m->d.err) {
+    set_error("hfd3_steps_profiled: the mesh was built host-only");
+    return HFD_ERR_UNSUPPORTED;
   }
   ms[0] = ms[1] = ms[2] = 0.0;
   cudaEvent_t ev[4];
@@ -342,6 +358,7 @@ hfd_status hfd3_check(hfd3_mesh* m) {
     set_error("hfd3_check: null mesh");
     return HFD_ERR_ARG;
   }
+  if (!m->d.err) return HFD_OK;               // host-only mesh: nothing ran
   CK3(cudaDeviceSynchronize());
   unsigned w = 0;
   CK3(cudaMemcpy(&w, m->d.err, sizeof w, cudaMemcpyDeviceToHost));

@@ -24,7 +24,7 @@ class Options3(ctypes.Structure):
                 ("sens_lo", ctypes.c_double), ("sens_hi", ctypes.c_double),
                 ("harten", ctypes.c_double), ("sv_rtol", ctypes.c_double),
                 ("div_cond_min", ctypes.c_double), ("force_branch", ctypes.c_int32),
-                ("threads", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("host_only", ctypes.c_int32)]
 
 
 class MeshDesc3(ctypes.Structure):
@@ -76,7 +76,8 @@ def options3(**kw):
 
 class Mesh3:
     """A periodic tetrahedral mesh on the device (hfd3_mesh_*), built from a mesh dict with x,
-    y, z, tet, Lx, Ly, Lz (as made by synth.three_d.periodic_tet_box)."""
+    y, z, tet, Lx, Ly, Lz (as made by synth.three_d.periodic_tet_box).  host_only=1 builds the
+    host preprocessing alone (no GPU needed; prep_get and info work)."""
 
     def __init__(self, mesh, **opts):
         x = np.ascontiguousarray(mesh["x"], dtype=np.float64)

@@ -42,23 +42,54 @@ def test_library_exports_every_3d_entry_point(pkg):
     assert declared == set(hfd3d.EXPORTED)
 
 
-def test_3d_preprocessing_runs_on_the_host_and_matches_the_oracle_structure(pkg):
-    """hfd3_mesh_create's host preprocessing needs no GPU for its structure, but creating a
-    mesh uploads it; on a machine without a GPU the call fails with HFD_ERR_CUDA after the
-    preprocessing, which the binding reports as an error (never a silent fallback)."""
+def test_3d_host_preprocessing_matches_the_oracle(pkg):
+    """The 3D preprocessing built host-only (hfd3_options.host_only, no GPU) against the 3D
+    oracle on a 6^3 box: edges, stencils, ranks and two-level sets identical; frames and 3-node
+    weights to rounding; 5-node weights within their systems' conditioning; divergence rows to
+    1e-12 of each row's scale.  Device calls on a host-only mesh are refused."""
+    import ctypes
     from paper_2109_01286_gb300 import hfd3d
+    from oracle import hfd3d as O
     from synth import three_d as T
-    m = T.periodic_tet_box(6, 6, 6, 1.0, 1.0, 1.0, seed=1)
-    try:
-        import torch
-        has_gpu = torch.cuda.is_available()
-    except ImportError:
-        has_gpu = False
-    if has_gpu:
-        pytest.skip("covered by the GPU tests")
-    with pytest.raises(pkg.HfdError) as e:
-        hfd3d.Mesh3(m)
-    assert e.value.status == 5
+    m = T.periodic_tet_box(6, 6, 6, 10.0, 10.0, 10.0, seed=3)
+    P = O.prepare(m)
+    mesh = hfd3d.Mesh3(m, host_only=1)
+    topo = P.topo
+    V = topo["V"]
+    assert np.array_equal(mesh.prep_get("edges").reshape(-1, 2), topo["edges"])
+    assert np.array_equal(mesh.prep_get("sten").reshape(-1, 6), P.stencil)
+    assert np.array_equal(mesh.prep_get("rank").reshape(-1, 2), P.rank)
+    np.testing.assert_allclose(mesh.prep_get("frame").reshape(-1, 9),
+                               np.concatenate([P.normal, P.t1, P.t2], 1), atol=1e-15)
+    np.testing.assert_allclose(mesh.prep_get("w3").reshape(P.w3.shape), P.w3, rtol=1e-12, atol=1e-14)
+    d5 = np.abs(mesh.prep_get("w5").reshape(P.w5.shape) - P.w5).max(axis=(1, 2))
+    assert d5.max() < 1e-4 and np.median(d5) < 1e-9
+    vptr, vidx = mesh.prep_get("vptr"), mesh.prep_get("vidx")
+    eptr, eidx = mesh.prep_get("eptr"), mesh.prep_get("eidx")
+    cv, ce = mesh.prep_get("cv").reshape(-1, 4, 3), mesh.prep_get("ce").reshape(-1, 4)
+    for v in range(V):
+        verts, edges = O.vertex_stencil(topo, v)
+        assert np.array_equal(vidx[vptr[v]:vptr[v + 1]], verts)
+        assert np.array_equal(eidx[eptr[v]:eptr[v + 1]], edges)
+        if v % 5:
+            continue
+        for r in range(4):
+            row = P.D[r].getrow(v).toarray()[0]
+            ref = np.concatenate([row[(3 * verts[:, None] + np.arange(3)).ravel()], row[3 * V + edges]])
+            lib = np.concatenate([cv[vptr[v]:vptr[v + 1], r, :].ravel(), ce[eptr[v]:eptr[v + 1], r]])
+            assert np.abs(lib - ref).max() < 1e-12 * np.abs(ref).max()
+    info = mesh.info()
+    assert info["nv"] == V and info["nedges"] == len(topo["edges"])
+    assert info["div_nv_total"] == len(vidx) and info["div_ne_total"] == len(eidx)
+    # no device arrays: residual and steps are refused before any pointer is used
+    lib = pkg.hfd._lib
+    fake = ctypes.c_void_p(16)
+    assert lib.hfd3_residual(mesh._h, fake, ctypes.c_void_p(32), None) == 9
+    assert lib.hfd3_steps(mesh._h, fake, 0.1, 1, None) == 9
+    assert lib.hfd3_check(mesh._h) == 0
+    # coefficient arrays can still be replaced on the host
+    mesh.prep_set("w5", P.w5)
+    assert np.array_equal(mesh.prep_get("w5").reshape(P.w5.shape), P.w5)
 
 
 def test_bounds_checked_build_exports_the_same_entry_points(pkg):
