@@ -1,12 +1,13 @@
 // CUDA kernels (sm_103a) of the three-dimensional extension of the Hermite FD residual and
-// SSP-RK3 step, FP64.  Per Runge-Kutta stage:
+// SSP-RK3 step; FP64 state, fluxes and sums.  Per Runge-Kutta stage:
 //   k3_vertex  one thread per vertex: the vertex-major copy of the 20 unknowns and the analytic
 //              flux vectors F, G, K (Sec. 2.3, vertex fluxes, in 3D);
 //   k3_edge    one thread per edge: Alg. 1 in 3D (Roe average of the edge ends, five-wave
-//              characteristic projection along the edge, uniform WENO5 weights as the sensor,
-//              5-node Hermite value or weighted 3-node value per component and side,
+//              characteristic projection along the edge, uniform WENO5 weights as the sensor --
+//              taken in FP32 and again in FP64 inside a band around each threshold -- 5-node
+//              Hermite value or weighted 3-node value per component and side,
 //              back-projection, positivity fallback) and Roe's flux with Harten's fix;
-//   k3_div     one thread per vertex: the CSR gather of the least-squares divergence rows
+//   k3_div     1, 2 or 4 lanes per vertex: the CSR gather of the least-squares divergence rows
 //              d_0, d_x, d_y, d_z over the vertex fluxes and edge fluxes (Eq.
 //              (flux_polynomials) in 3D), fused with the SSP-RK3 stage update.
 // The characteristic projection uses the closed forms of the left and right eigenvectors of
